@@ -1,0 +1,224 @@
+"""Seeded synthetic inputs for detector tomography (shared by the oracle tests,
+the GPU tests and the benchmark).
+
+This module simulates the *experiment*, not the reconstruction: it builds a
+detector's true POVM matrix Theta_true (M photon numbers x N outcomes) from a
+physical click-detector model, chooses coherent-probe intensities lambda_d, and
+produces measured outcome frequencies P (D x N) by evaluating the probes'
+photon-number statistics with ``scipy.stats.poisson`` and drawing multinomial
+counts with numpy's PCG64.  It contains none of the solver's arithmetic
+(objective, gradients, Hessian products, projections, Newton/CG/line-search
+steps), so a mistake in either solver cannot be hidden by shared code here.
+
+Detector model (a reading of the paper's multiplexed click detector, Sec.
+"Detector under test"; the synthetic configurations use uniform bins):
+B = N - 1 bins, outcome n = number of clicked bins.  Photons arrive one at a
+time; each survives loss with probability eta and lands in a uniformly chosen
+bin (a new click if that bin was still dark).  With probability ``crosstalk`` a
+detected photon fires one extra uniformly chosen bin.  After all photons, each
+still-dark bin fires a dark count with probability ``p_dark``.  Theta_true[i, :]
+is the distribution of the clicked-bin count after i photons.  The chain is a
+product of stochastic matrices (no alternating sums), so it is stable for any i.
+
+Probe grid: lambda_d = X * d / (D - 1), d = 0..D-1, endpoints included.
+
+Noise: P_d = multinomial(shots, q_d / sum(q_d)) / shots, where
+q_d = sum_i Poisson(i; lambda_d) Theta_true[i, :] over i < M.  ``shots=None``
+gives the noise-free q_d (not renormalised).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+BASE_SEED = 2404028440
+
+
+def probe_intensities(D: int, X: float) -> np.ndarray:
+    """lambda_d = X*d/(D-1) for d = 0..D-1 (D == 1 gives [0])."""
+    if D == 1:
+        return np.zeros(1)
+    return X * np.arange(D, dtype=np.float64) / (D - 1)
+
+
+def quadratic_intensities(D: int, scale: float = 1.0) -> np.ndarray:
+    """lambda_d = scale * d^2, the paper's experimental probe spacing."""
+    return scale * np.arange(D, dtype=np.float64) ** 2
+
+
+def _photon_transition(B: int, eta: float, crosstalk: float) -> np.ndarray:
+    """(B+1)x(B+1) row-stochastic matrix of one arriving photon on the
+    clicked-bin count c."""
+    T = np.zeros((B + 1, B + 1))
+    for c in range(B + 1):
+        # photon lost
+        T[c, c] += 1.0 - eta
+        # photon detected: lands in a dark bin with probability (B-c)/B
+        p_new = (B - c) / B
+        for c1, w in ((c + 1, p_new), (c, 1.0 - p_new)):
+            if w == 0.0:
+                continue
+            # no crosstalk
+            T[c, c1] += eta * w * (1.0 - crosstalk)
+            # crosstalk: one extra click in a uniformly chosen bin
+            if crosstalk > 0.0:
+                p_x = (B - c1) / B
+                if p_x > 0.0:
+                    T[c, c1 + 1] += eta * w * crosstalk * p_x
+                T[c, c1] += eta * w * crosstalk * (1.0 - p_x)
+    return T
+
+
+def _dark_matrix(B: int, p_dark: float) -> np.ndarray:
+    """(B+1)x(B+1) matrix: c -> c + Binomial(B - c, p_dark)."""
+    K = np.zeros((B + 1, B + 1))
+    for c in range(B + 1):
+        k = np.arange(B - c + 1)
+        logc = (math.lgamma(B - c + 1) - np.array([math.lgamma(j + 1) for j in k])
+                - np.array([math.lgamma(B - c - j + 1) for j in k]))
+        if p_dark == 0.0:
+            w = (k == 0).astype(np.float64)
+        else:
+            w = np.exp(logc + k * math.log(p_dark) + (B - c - k) * math.log1p(-p_dark))
+        K[c, c:] = w
+    return K
+
+
+def detector_povm(M: int, bins: int, eta: float, p_dark: float = 0.0,
+                  crosstalk: float = 0.0) -> np.ndarray:
+    """Theta_true, shape (M, bins+1), rows on the probability simplex."""
+    B = int(bins)
+    T = _photon_transition(B, eta, crosstalk)
+    K = _dark_matrix(B, p_dark)
+    theta = np.empty((M, B + 1))
+    row = np.zeros(B + 1)
+    row[0] = 1.0
+    i = 0
+    while i < M:
+        theta[i] = row
+        nxt = row @ T
+        i += 1
+        # once the chain has reached its absorbing state to the last bit,
+        # every later row is identical
+        if np.array_equal(nxt, row):
+            theta[i:] = row
+            break
+        row = nxt
+    theta = theta @ K
+    # rows are stochastic up to rounding; renormalise exactly
+    theta = np.maximum(theta, 0.0)
+    theta /= theta.sum(axis=1, keepdims=True)
+    return theta
+
+
+def outcome_probabilities(lam: np.ndarray, theta: np.ndarray,
+                          width_sigmas: float = 14.0) -> np.ndarray:
+    """q_d = sum_{i<M} Poisson(i; lambda_d) Theta[i, :], using scipy's pmf on
+    the photon numbers within +-width_sigmas*sqrt(lambda)+40 of lambda (the
+    mass outside is below 1e-40)."""
+    from scipy.stats import poisson
+
+    M, N = theta.shape
+    D = lam.shape[0]
+    q = np.zeros((D, N))
+    # rows identical from some index on: collapse the tail into one sf term
+    last_change = M - 1
+    while last_change > 0 and np.array_equal(theta[last_change], theta[last_change - 1]):
+        last_change -= 1
+    for d in range(D):
+        l = float(lam[d])
+        s = math.sqrt(l)
+        a = max(0, int(math.floor(l - width_sigmas * s - 40)))
+        b = min(M - 1, int(math.ceil(l + width_sigmas * s + 40)))
+        if a > b:
+            continue
+        b_body = min(b, last_change - 1) if last_change < M - 1 else b
+        if b_body >= a:
+            i = np.arange(a, b_body + 1)
+            w = poisson.pmf(i, l)
+            q[d] += w @ theta[a:b_body + 1]
+        if last_change < M - 1 and b >= last_change:
+            start = max(a, last_change)
+            # mass on [start, M-1] of the constant tail row
+            mass = poisson.cdf(M - 1, l) - (poisson.cdf(start - 1, l) if start > 0 else 0.0)
+            if mass < 0.0:
+                mass = float(poisson.pmf(np.arange(start, min(M, start + 200000)), l).sum())
+            q[d] += mass * theta[last_change]
+    return q
+
+
+def sample_outcomes(q: np.ndarray, shots, rng: np.random.Generator) -> np.ndarray:
+    """Multinomial outcome frequencies per probe (shots=None: noise-free q)."""
+    if shots is None:
+        return q.copy()
+    P = np.empty_like(q)
+    for d in range(q.shape[0]):
+        p = np.maximum(q[d], 0.0)
+        p = p / p.sum()
+        P[d] = rng.multinomial(int(shots), p) / float(shots)
+    return P
+
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    M: int
+    N: int
+    D: int
+    lam: np.ndarray
+    P: np.ndarray
+    theta_true: np.ndarray
+    gamma: float
+    band_k: float
+    seed: int
+    shots: object
+
+    @property
+    def MN(self) -> int:
+        return self.M * self.N
+
+
+def make_workload(name: str, M: int, bins: int, eta: float, D: int, X: float,
+                  gamma: float, band_k: float, shots, seed: int,
+                  p_dark: float = 0.0, crosstalk: float = 0.0,
+                  lam: np.ndarray | None = None) -> Workload:
+    rng = np.random.Generator(np.random.PCG64(seed))
+    theta = detector_povm(M, bins, eta, p_dark=p_dark, crosstalk=crosstalk)
+    if lam is None:
+        lam = probe_intensities(D, X)
+    q = outcome_probabilities(lam, theta)
+    P = sample_outcomes(q, shots, rng)
+    return Workload(name, M, bins + 1, D, lam, P, theta, gamma, band_k, seed, shots)
+
+
+def config_c1(shots=1_000_000) -> Workload:
+    """Plain FP64 fit: M=64, N=9 (8-bin detector, eta=0.7), D=100 probes with
+    lambda linear in [0,30], 1e6 shots, gamma=1e-3, dense F."""
+    return make_workload("c1_M64_N9_D100", 64, 8, 0.7, 100, 30.0, 1e-3, 0.0,
+                         shots, BASE_SEED + 0)
+
+
+def config_c2(shots=10_000_000) -> Workload:
+    """FP64 vs FP32 fit: M=4096, N=128 (127 bins, eta=0.8, dark 1e-4/bin),
+    D=8192 probes with lambda linear in [0,3000], 1e7 shots, gamma=1e-2,
+    Poisson band +-10 sqrt(lambda)."""
+    return make_workload("c2_M4096_N128_D8192", 4096, 127, 0.8, 8192, 3000.0,
+                         1e-2, 10.0, shots, BASE_SEED + 1, p_dark=1e-4)
+
+
+def small_case(M=48, bins=7, eta=0.75, D=80, X=40.0, gamma=1e-3, band_k=10.0,
+               shots=100_000, seed=BASE_SEED + 77, p_dark=0.0, crosstalk=0.0):
+    """A scaled-down instance of the same construction (tests)."""
+    return make_workload(f"small_M{M}_N{bins+1}_D{D}", M, bins, eta, D, X, gamma,
+                         band_k, shots, seed, p_dark=p_dark, crosstalk=crosstalk)
+
+
+def random_feasible_theta(M: int, N: int, rng: np.random.Generator,
+                          sparsity: float = 0.3) -> np.ndarray:
+    """A random point of the row simplices with some exact zeros."""
+    x = rng.random((M, N))
+    x[rng.random((M, N)) < sparsity] = 0.0
+    x[np.arange(M), rng.integers(0, N, M)] += 0.5
+    return x / x.sum(axis=1, keepdims=True)
