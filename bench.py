@@ -1,0 +1,336 @@
+"""Benchmark: time-to-tolerance (relative objective gap 1e-8) and
+POVM-elem*iters/s of the detector-tomography solver on the synthetic
+M=4096, N=128, D=8192 workload (127-bin detector, efficiency 0.8, dark counts
+1e-4/bin, lambda linear in [0, 3000], 1e7 shots, gamma 1e-2, band
++-10 sqrt(lambda)).
+
+A step is one full two-stage solve (Algorithm 3) from Theta^(0) = 1/N until the
+objective is within 1e-8 (relative) of the optimum certified by the FP64
+oracle (tests/golden/fstar_c2.json, written by tests/golden/make_fstar.py).
+The chosen form uses FP32 band contractions with a double-precision residual;
+the plain FP64 GPU solver is timed beside it.  Prints one JSON line.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "time-to-tolerance (rel. obj gap 1e-8) and POVM-elem·iters/s, chosen vs plain"
+UNIT = "POVM-elem*iters/s"
+GAP = 1e-8
+WORKLOAD = "c2: M=4096 N=128 D=8192, 127-bin eta=0.8 dark=1e-4, lambda lin [0,3000], 1e7 shots, gamma=1e-2, band +-10sqrt(lambda)"
+
+
+def load_fstar():
+    with open(os.path.join(ROOT, "tests", "golden", "fstar_c2.json")) as fh:
+        return json.load(fh)
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.dev)], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self._t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if os.environ.get("TOMO_BENCH_BACKEND") != "gloo" else "gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, x: float) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- reference
+def run_reference(args, world, rank):
+    """The FP64 CPU oracle as it stands, on the host cores: each step is a
+    bounded sample of the same solve (the first Newton iteration from
+    Theta^(0) = 1/N)."""
+    if rank != 0:
+        return
+    import oracle
+    w = workloads.config_c2()
+    pr = oracle.Problem.from_workload(w)
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        pr.fit(w.P, max_newton=1, eps_kkt=0.0)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        pr.fit(w.P, max_newton=1, eps_kkt=0.0)
+        times.append(time.perf_counter() - t0)
+    T = sum(times)
+    value = w.M * w.N * args.steps / T
+    cores = oracle.num_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "global_batch": 1, "seq_len": w.M,
+                   "parallelism": "host cores (OpenMP)", "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "first Newton iteration of the c2 solve per step (FP64 C oracle)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="chosen", choices=["chosen", "reference"])
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 solve")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
+    args = ap.parse_args()
+    world, rank, local = dist_init()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+
+    import torch
+
+    import paper_2404_02844_gb300 as tomo
+    from paper_2404_02844_gb300 import build as tomo_build
+
+    tomo_build.build()
+    torch.cuda.set_device(local)
+    gold = load_fstar()
+    f_star = gold["f_star"]
+    f_target = f_star * (1.0 + 0.5 * GAP)
+
+    w = workloads.config_c2()
+    M, N, D = w.M, w.N, w.D
+    P = torch.from_numpy(w.P).cuda()
+    l2_flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def flush():
+        l2_flush.fill_(1.0)
+
+    def solve(plan, Pbuf, Theta=None, profile=0):
+        return plan.fit(Pbuf, Theta, f_target=f_target, profile=profile)
+
+    chosen = tomo.Plan.from_workload(w, precision="fp32")
+    lo, hi = chosen.bands()
+    nnz = int(np.sum(np.maximum(hi - lo + 1, 0)))
+
+    for _ in range(args.warmup):
+        solve(chosen, P)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K full solves, L2 flushed before each -------------
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    times, iters, reps = [], [], []
+    launches0 = tomo.tomo_kernel_launches()
+    for _ in range(args.steps):
+        flush()
+        torch.cuda.synchronize()
+        barrier(world)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        Th, rep = solve(chosen, P, profile=1)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        times.append(ev0.elapsed_time(ev1) / 1e3)
+        iters.append(rep["iters_s1"] + rep["iters_s2"])
+        reps.append(rep)
+    launches = tomo.tomo_kernel_launches() - launches0
+    clk = clocks.stop()
+    barrier(world)
+    T = max_over_ranks(world, sum(times))
+    # tolerance check (excluded from the timing): FP64 objective of the result
+    f_final = chosen.objective(P, Th)
+    gap = (f_final - f_star) / f_star
+    units = M * N * sum(iters) * world
+    value = units / T
+    ttt = T / args.steps
+
+    # dominant kernel: FP32 forward band contraction, timed live with CUDA
+    # events on the plan stream inside the timed solves
+    fwd_ms = sum(r["fwd_ms"] for r in reps) / max(1, sum(r["fwd_count"] for r in reps))
+    adj_ms = sum(r["adj_ms"] for r in reps) / max(1, sum(r["adj_count"] for r in reps))
+    flops = 2.0 * nnz * N
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    peaks = measured_peaks()
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    alu_peak = sms * 128 * 2 * sm_max * 1e6 / 1e12  # FP32 FMA lanes x 2 flop x clock
+    achieved = flops / (fwd_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": achieved / alu_peak, "traffic": None,
+                "kernel": "k_forward<float> (F p, CG)", "avg_launch_ms": fwd_ms,
+                "algorithmic_flops_per_launch": flops,
+                "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz",
+                "adjoint": {"avg_launch_ms": adj_ms,
+                            "achieved": flops / (adj_ms * 1e-3) / 1e12}}
+
+    # ---- end to end through the C ABI with host buffers ------------------
+    P_host = torch.from_numpy(w.P).pin_memory().numpy()
+    Th_host = torch.empty((M, N), dtype=torch.float64).pin_memory().numpy()
+    e2e_t = []
+    for _ in range(args.steps):
+        flush()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, rep_e = chosen.fit(P_host, Th_host, f_target=f_target, warm_start=0)
+        e2e_t.append(time.perf_counter() - t0)
+        iters_e = rep_e["iters_s1"] + rep_e["iters_s2"]
+    e2e_T = max_over_ranks(world, sum(e2e_t))
+    e2e_value = M * N * iters_e * args.steps * world / e2e_T
+
+    # ---- plain FP64 GPU solver, same workload ----------------------------
+    plain = None
+    if not args.no_plain:
+        with tomo.Plan.from_workload(w, precision="fp64") as pl64:
+            flush()
+            torch.cuda.synchronize()
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            Th64, rep64 = pl64.fit(P, f_target=f_target)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            t64 = ev0.elapsed_time(ev1) / 1e3
+            f64 = pl64.objective(P, Th64)
+        it64 = rep64["iters_s1"] + rep64["iters_s2"]
+        plain = {"time_to_tolerance_s": t64, "value": M * N * it64 / t64, "unit": UNIT,
+                 "newton_iters": it64, "cg_total": rep64["cg_total"],
+                 "rel_gap": (f64 - f_star) / f_star, "stop": rep64["stop_name"],
+                 "chosen_speedup": t64 / ttt}
+
+    # ---- CPU baseline: the oracle on a bounded sample -----------------------
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        import oracle
+        pr = oracle.Problem.from_workload(w)
+        t0 = time.perf_counter()
+        _, rep_c, _ = pr.fit(w.P, max_newton=2, eps_kkt=0.0)
+        tc = time.perf_counter() - t0
+        cpu = {"value": M * N * 2 / tc, "unit": UNIT, "cores": oracle.num_threads(),
+               "kind": "oracle",
+               "sample": f"first 2 Newton iterations of the same solve ({rep_c['cg_total']} CG "
+                         f"products), FP64 C oracle, {tc:.1f}s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * ttt, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "fp32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "global_batch": world, "seq_len": M,
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "form": "chosen: FP32 band contractions, FP64 residual/objective/reductions",
+                       "l2": "flushed (512 MB write) before every timed solve"},
+            "time_to_tolerance_s": ttt,
+            "rel_gap": gap,
+            "newton_iters": iters,
+            "cg_total": [r["cg_total"] for r in reps],
+            "stop": reps[-1]["stop_name"],
+            "plain_fp64": plain,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": D * N * 8,
+                    "d2h_bytes_per_step": M * N * 8,
+                    "time_to_tolerance_s": e2e_T / args.steps},
+            "clocks": clk,
+            "gpu_launches": launches,
+        }
+        print(json.dumps(line), flush=True)
+    chosen.close()
+
+
+if __name__ == "__main__":
+    main()

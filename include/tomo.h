@@ -1,0 +1,205 @@
+/*
+ * tomo.h -- C ABI of the GB300 detector-tomography solver.
+ *
+ * The library reconstructs the diagonal POVM matrix Theta (M photon numbers x
+ * N outcomes, row-major) of a phase-insensitive detector from measured outcome
+ * frequencies P (D coherent probes x N, row-major) by solving
+ *
+ *     min_Theta  ||P - F Theta||_2^2 + gamma sum_n sum_{i=0}^{M-2}
+ *                (Theta_{i,n} - Theta_{i+1,n})^2
+ *     subject to Theta_{i,n} >= 0,  sum_n Theta_{i,n} = 1 for every i,
+ *
+ * (Schapeler et al., arXiv 2404.02844: Eq. min, Eq. regul), where
+ * F_{d,i} = lambda_d^i e^{-lambda_d} / i! (Eq. Fmatrix) is never stored: the
+ * kernels regenerate it in log space inside every band contraction.  The
+ * solver is the paper's two-stage, two-metric projected truncated Newton
+ * method (App. B, Algorithms 1-3).
+ *
+ * Conventions for every entry point:
+ *   - Return a tomo_status; nothing aborts, throws or exits across the ABI.
+ *     tomo_last_error() gives a message for the last failure on this thread.
+ *   - Matrices are dense, row-major, double precision, no padding.
+ *   - "device" pointers are CUDA global-memory pointers of the current device;
+ *     entry points documented as "host or device" accept either and detect the
+ *     kind with cudaPointerGetAttributes (host buffers are staged through
+ *     plan-owned device memory).
+ *   - Work is ordered on the plan's stream; calls return after the results
+ *     they report are complete (device outputs are complete on return).
+ *   - The caller keeps ownership of every buffer it passes; the plan owns its
+ *     workspaces and frees them in tomo_plan_destroy.
+ *   - A plan is not thread-safe: one call at a time per plan.
+ */
+#ifndef TOMO_H
+#define TOMO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TOMO_OK = 0,
+    TOMO_EINVAL = 1,     /* invalid argument (sizes, non-finite lambda, NULL) */
+    TOMO_ENOMEM = 2,     /* device or host allocation failed */
+    TOMO_ECUDA = 3,      /* a CUDA runtime call failed */
+    TOMO_ENOTCONV = 4,   /* iteration cap reached before the stopping rule */
+    TOMO_ETIMEOUT = 5,   /* reserved: a bounded device wait gave up */
+    TOMO_ENONFINITE = 6  /* P or Theta holds NaN/Inf, or the objective became non-finite */
+} tomo_status;
+
+/* Arithmetic of the band contractions F X and F^T Y.
+ *   FP64: every product in double ("plain" solver): the objective of every
+ *         line-search trial is evaluated directly, f = ||F Theta' - P||^2 + g.
+ *   FP32: products in single precision with FP32 accumulation; the residual
+ *         R = F Theta - P is kept in double, refreshed by a double product
+ *         every refresh_every Newton iterations and otherwise updated as
+ *         R <- R + F s for each accepted step s; line searches use the exact
+ *         quadratic expansion f(Theta + s) - f(Theta) = 2<R, F s> + ||F s||^2
+ *         + g(Theta + s) - g(Theta) reduced in double. */
+typedef enum { TOMO_PREC_FP64 = 0, TOMO_PREC_FP32 = 1 } tomo_precision;
+
+typedef struct tomo_plan_s *tomo_plan_t;
+
+/* Problem descriptor (Eq. min, Eq. Fmatrix, Eq. regul). */
+typedef struct {
+    int64_t M;             /* photon-number cutoff: i = 0..M-1, 1 <= M <= 2^30 */
+    int64_t N;             /* outcomes, 2 <= N <= 1024 */
+    int64_t D;             /* probes, 1 <= D <= 2^30 */
+    const double *lambda;  /* HOST array of D mean photon numbers |alpha_d|^2,
+                              finite, >= 0 and non-decreasing (probes sorted by
+                              intensity); copied by tomo_plan */
+    double band_k;         /* Poisson band half-width in standard deviations:
+                              F_{d,i} is kept for lo_d <= i <= hi_d with
+                              lo_d = max(0, floor(lambda - k sqrt(lambda))),
+                              hi_d = min(M-1, max(16, ceil(lambda + k sqrt(lambda))));
+                              band_k <= 0 keeps every i (dense F) */
+    double gamma;          /* regularisation weight gamma >= 0 (Eq. regul) */
+    int32_t precision;     /* tomo_precision */
+    int32_t reserved;
+    void *stream;          /* cudaStream_t to order work on; NULL: the plan
+                              creates and owns a non-blocking stream */
+    uint32_t flags;        /* must be 0 */
+} tomo_desc;
+
+/* Builds a plan: validates the descriptor, computes the probe bands, the
+ * log-space Poisson anchor table, the contraction tile schedule and the
+ * Hessian diagonal on the device, and allocates every workspace (about
+ * (3 D N + 13 M N) doubles).  Invalid input gives TOMO_EINVAL and leaves
+ * *out == NULL.  (Eq. Fmatrix; Table ops "diagonal of Hessian".) */
+tomo_status tomo_plan(tomo_plan_t *out, const tomo_desc *desc);
+
+/* Frees the plan and everything it owns.  NULL is accepted. */
+void tomo_plan_destroy(tomo_plan_t plan);
+
+/* Objective value (Table ops "objective value"; Eq. min + Eq. regul):
+ * *f_host = ||P - F Theta||^2 + gamma sum (Theta_{i,n} - Theta_{i+1,n})^2,
+ * always in double.  P (D x N) and Theta (M x N) are host or device.  If
+ * grad is not NULL it receives G = 2 F^T (F Theta - P) + 2 gamma L Theta
+ * (M x N, same kind of memory as Theta), computed with the plan's
+ * precision for F^T R and double for the residual. */
+tomo_status tomo_objective(tomo_plan_t plan, const double *P, const double *Theta,
+                           double *f_host, double *grad);
+
+/* Solver options; tomo_fit_opts_default fills the defaults shown. */
+typedef struct {
+    double eps_kkt;        /* 1e-10: stop when the KKT residual of App. B,
+                              sqrt(mean (Theta (G + lambda_i))^2) with
+                              lambda_i = max(0, -min_n G_{i,n}), is <= eps_kkt */
+    double eps_bar;        /* 1e-6: eps_k = min(eps_bar, w_k) in the index set I */
+    double beta;           /* 0.75: backtracking factor (App. B) */
+    double c;              /* 0.1: Armijo constant (App. B) */
+    double switch_tol;     /* 1e-4: stage-1 -> stage-2 switch threshold (App. B) */
+    double f_target;       /* 0: off; > 0: stop as soon as f <= f_target
+                              (checked with a double-precision residual) */
+    int32_t max_newton;    /* 1000: Newton iterations, both stages together */
+    int32_t max_stage1;    /* 200: stage-1 iterations */
+    int32_t max_cg;        /* 50: Hessian products per Newton iteration */
+    int32_t ls_max;        /* 50: backtracking steps per line search */
+    int32_t start_stage;   /* 1: Algorithm 3; 2: stage 2 only (Algorithm 1) */
+    int32_t warm_start;    /* 0: Theta^(0) = 1/N; 1: start from Theta as passed */
+    int32_t stall_iters;   /* 5: stop after this many iterations without decrease */
+    int32_t refresh_every; /* 8: FP32 plans recompute R in double this often */
+    int32_t profile;       /* 0; 1: time every band contraction of the CG loop
+                              with CUDA events on the plan stream (report fields
+                              fwd_ms / adj_ms); adds no synchronisation */
+} tomo_fit_opts;
+
+/* Result of a fit. */
+typedef struct {
+    double f;              /* final objective (double-precision residual) */
+    double kkt;            /* final KKT residual */
+    double time_ms;        /* wall time of the solve on the host clock */
+    int32_t iters_s1, iters_s2;  /* Newton iterations per stage */
+    int32_t cg_total;      /* Hessian products in CG */
+    int32_t ls_total;      /* line-search trials */
+    int32_t refreshes;     /* double-precision residual recomputations */
+    int32_t stop;          /* 0 KKT reached, 1 f_target reached, 2 iteration cap,
+                              3 stagnated (no decrease / line search failed) */
+    int32_t stage_end;     /* stage at exit */
+    int32_t kernels;       /* kernels launched by this call */
+    int32_t fwd_count;     /* profiled CG products F p (opts.profile) */
+    int32_t adj_count;     /* profiled CG products F^T (F p) */
+    double fwd_ms;         /* summed device time of those launches */
+    double adj_ms;
+} tomo_fit_report;
+
+void tomo_fit_opts_default(tomo_fit_opts *opts);
+
+/* Two-stage two-metric projected truncated Newton fit (Algorithm 3: stage 1
+ * = Algorithm 2 with the row-wise simplex projection P_{S^M}, stage 2 =
+ * Algorithm 1 with the row-maximum transformation).  P (D x N) is read,
+ * Theta (M x N) is read when opts->warm_start and always overwritten with
+ * the result; both host or device.  opts may be NULL (defaults); report may
+ * be NULL.  Theta is on the row simplices on every return except
+ * TOMO_EINVAL.  Returns TOMO_OK for stop codes 0, 1 and 3, TOMO_ENOTCONV for
+ * the iteration cap. */
+tomo_status tomo_fit(tomo_plan_t plan, const double *P, double *Theta,
+                     const tomo_fit_opts *opts, tomo_fit_report *report);
+
+/* ---- single steps of the hot path (device pointers only) ----------------
+ * Exposed so that every step can be checked on its own; the solver calls the
+ * same kernels. */
+
+/* O = F X (Table ops, the F Pi product of the objective): X M x N -> O D x N,
+ * computed in the plan's precision, stored in double. */
+tomo_status tomo_apply_F(tomo_plan_t plan, const double *X, double *O);
+
+/* Z = F^T Y: Y D x N -> Z M x N, plan precision, stored in double. */
+tomo_status tomo_apply_Ft(tomo_plan_t plan, const double *Y, double *Z);
+
+/* Hessian product (Table ops): HV = 2 F^T F V + 2 gamma L V, M x N. */
+tomo_status tomo_hvp(tomo_plan_t plan, const double *V, double *HV);
+
+/* Hessian diagonal h_i = 2 sum_d F_{d,i}^2 + 2 gamma L_ii (Table ops), M
+ * doubles, always computed in double at plan time. */
+tomo_status tomo_hess_diag(tomo_plan_t plan, double *h);
+
+/* Row-wise projection onto the probability simplex (Eq. Mp1_proj):
+ * Y_i = argmin_{y >= 0, sum y = 1} ||X_i - y||, M rows of N; double. */
+tomo_status tomo_project_simplex(tomo_plan_t plan, const double *X, double *Y);
+
+/* KKT residual of App. B for (Theta, G), both M x N device; double. */
+tomo_status tomo_kkt(tomo_plan_t plan, const double *Theta, const double *G,
+                     double *kkt_host);
+
+/* Poisson weights F_{d,i} as the kernels generate them, for `count` pairs
+ * (d[k], i[k]) given in HOST arrays; out_host receives double values in the
+ * plan's precision (0 outside the band). */
+tomo_status tomo_poisson_weights(tomo_plan_t plan, const int64_t *d, const int64_t *i,
+                                 int64_t count, double *out_host);
+
+/* Band bounds lo_d, hi_d as computed by the plan (HOST arrays of D). */
+tomo_status tomo_bands(tomo_plan_t plan, int64_t *lo_host, int64_t *hi_host);
+
+/* Kernel launches made by this library since it was loaded (all threads,
+ * all entry points), for launch accounting. */
+int64_t tomo_kernel_launches(void);
+
+/* Message of the last failure on the calling thread ("" if none). */
+const char *tomo_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TOMO_H */

@@ -35,7 +35,10 @@ def build(force: bool = False) -> str:
             and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
         return _LIB
     tmp = _LIB + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11",
+    # -ffp-contract=off: products and sums are rounded as written (no fused
+    # multiply-add), so integer decisions such as the band bounds are those of
+    # the plain IEEE evaluation on every host architecture
+    cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11", "-ffp-contract=off",
            "-o", tmp, _SRC, "-lm"]
     subprocess.check_call(cmd)
     os.replace(tmp, _LIB)
@@ -73,6 +76,8 @@ def lib():
         L.orc_bands.argtypes = [c_ptr, c_ptr, c_ptr]
         for name in ("orc_apply_F", "orc_apply_Ft", "orc_hvp"):
             getattr(L, name).argtypes = [c_ptr, c_ptr, c_ptr]
+        L.orc_apply_F_rows.argtypes = [c_ptr, c_ptr, c_ptr, c_i64, c_ptr]
+        L.orc_apply_Ft_rows.argtypes = [c_ptr, c_ptr, c_ptr, c_i64, c_ptr]
         L.orc_regulariser.restype = c_dbl
         L.orc_regulariser.argtypes = [c_ptr, c_ptr]
         L.orc_objective.restype = c_dbl
@@ -174,6 +179,21 @@ class Problem:
         Z = np.empty((self.M, self.N))
         lib().orc_apply_Ft(self._h, _p(Y), _p(Z))
         return Z
+
+    def apply_F_rows(self, X, rows) -> np.ndarray:
+        """Selected rows of F X (X must be C-contiguous M x N float64)."""
+        X = _f64(X)
+        rows = np.ascontiguousarray(rows, dtype=np.int64)
+        out = np.empty((rows.shape[0], self.N))
+        lib().orc_apply_F_rows(self._h, _p(X), _p(rows), rows.shape[0], _p(out))
+        return out
+
+    def apply_Ft_rows(self, Y, rows) -> np.ndarray:
+        Y = _f64(Y)
+        rows = np.ascontiguousarray(rows, dtype=np.int64)
+        out = np.empty((rows.shape[0], self.N))
+        lib().orc_apply_Ft_rows(self._h, _p(Y), _p(rows), rows.shape[0], _p(out))
+        return out
 
     def regulariser(self, X) -> float:
         return lib().orc_regulariser(self._h, _p(_f64(X)))

@@ -115,12 +115,17 @@ ORC_API orc_problem *orc_create(int64_t M, int64_t N, int64_t D, const double *l
         int64_t cnt = p->hi[d] >= p->lo[d] ? p->hi[d] - p->lo[d] + 1 : 0;
         p->off[d + 1] = p->off[d] + cnt;
     }
-    for (int64_t i = 0; i < M; ++i) { p->dlo[i] = D; p->dhi[i] = -1; }
-    for (int64_t d = 0; d < D; ++d)
-        for (int64_t i = p->lo[d]; i <= p->hi[d]; ++i) {
-            if (d < p->dlo[i]) p->dlo[i] = d;
-            if (d > p->dhi[i]) p->dhi[i] = d;
-        }
+    if (store_F) {
+        for (int64_t i = 0; i < M; ++i) { p->dlo[i] = D; p->dhi[i] = -1; }
+        for (int64_t d = 0; d < D; ++d)
+            for (int64_t i = p->lo[d]; i <= p->hi[d]; ++i) {
+                if (d < p->dlo[i]) p->dlo[i] = d;
+                if (d > p->dhi[i]) p->dhi[i] = d;
+            }
+    } else {
+        /* lazy mode (sampled outputs only): scan every probe */
+        for (int64_t i = 0; i < M; ++i) { p->dlo[i] = 0; p->dhi[i] = D - 1; }
+    }
     if (store_F) {
         p->F = (double *)malloc(sizeof(double) * (p->off[D] > 0 ? p->off[D] : 1));
         if (!p->F) { free(p); return NULL; }
@@ -169,6 +174,43 @@ ORC_API void orc_apply_F(const orc_problem *p, const double *X, double *O)
             double f = Fval(p, d, i);
             const double *x = X + i * N;
             for (int64_t n = 0; n < N; ++n) o[n] += f * x[n];
+        }
+    }
+}
+
+/* Rows `rows[k]` of O = F X only (out: nrows x N). */
+ORC_API void orc_apply_F_rows(const orc_problem *p, const double *X, const int64_t *rows,
+                              int64_t nrows, double *out)
+{
+    const int64_t N = p->N;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t k = 0; k < nrows; ++k) {
+        const int64_t d = rows[k];
+        double *o = out + k * N;
+        for (int64_t n = 0; n < N; ++n) o[n] = 0.0;
+        for (int64_t i = p->lo[d]; i <= p->hi[d]; ++i) {
+            double f = Fval(p, d, i);
+            const double *x = X + i * N;
+            for (int64_t n = 0; n < N; ++n) o[n] += f * x[n];
+        }
+    }
+}
+
+/* Rows `rows[k]` of Z = F^T Y only (out: nrows x N). */
+ORC_API void orc_apply_Ft_rows(const orc_problem *p, const double *Y, const int64_t *rows,
+                               int64_t nrows, double *out)
+{
+    const int64_t N = p->N;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t k = 0; k < nrows; ++k) {
+        const int64_t i = rows[k];
+        double *z = out + k * N;
+        for (int64_t n = 0; n < N; ++n) z[n] = 0.0;
+        for (int64_t d = p->dlo[i]; d <= p->dhi[i]; ++d) {
+            if (i < p->lo[d] || i > p->hi[d]) continue;
+            double f = Fval(p, d, i);
+            const double *y = Y + d * N;
+            for (int64_t n = 0; n < N; ++n) z[n] += f * y[n];
         }
     }
 }

@@ -1,0 +1,323 @@
+"""GB300 detector-tomography solver: Python binding of the C ABI in
+include/tomo.h (libtomo.so, hand-written CUDA for sm_103a).
+
+This module only marshals arguments: every step of the solve runs in the
+library's kernels.  There is no CPU fallback -- if libtomo.so is missing or a
+call fails, an exception is raised.
+
+The functions ``tomo_plan``, ``tomo_objective``, ``tomo_fit``, ... carry the
+names of the C entry points; :class:`Plan` wraps them for torch CUDA tensors
+(float64, contiguous; device memory) and numpy arrays (host memory).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB as _LIB_PATH
+
+__all__ = ["Plan", "TomoError", "lib", "tomo_plan", "tomo_plan_destroy", "tomo_objective",
+           "tomo_fit", "tomo_fit_opts_default", "tomo_apply_F", "tomo_apply_Ft", "tomo_hvp",
+           "tomo_hess_diag", "tomo_project_simplex", "tomo_kkt", "tomo_poisson_weights",
+           "tomo_bands", "tomo_kernel_launches", "tomo_last_error", "PREC_FP64", "PREC_FP32",
+           "STATUS", "STOP"]
+
+PREC_FP64 = 0
+PREC_FP32 = 1
+STATUS = {0: "TOMO_OK", 1: "TOMO_EINVAL", 2: "TOMO_ENOMEM", 3: "TOMO_ECUDA",
+          4: "TOMO_ENOTCONV", 5: "TOMO_ETIMEOUT", 6: "TOMO_ENONFINITE"}
+STOP = {0: "kkt", 1: "f_target", 2: "iteration_cap", 3: "stagnated"}
+
+c_i32, c_i64, c_u32, c_dbl, c_ptr = (ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32,
+                                     ctypes.c_double, ctypes.c_void_p)
+
+
+class tomo_desc(ctypes.Structure):
+    _fields_ = [("M", c_i64), ("N", c_i64), ("D", c_i64), ("lambda_", c_ptr),
+                ("band_k", c_dbl), ("gamma", c_dbl), ("precision", c_i32),
+                ("reserved", c_i32), ("stream", c_ptr), ("flags", c_u32)]
+
+
+class tomo_fit_opts(ctypes.Structure):
+    _fields_ = [("eps_kkt", c_dbl), ("eps_bar", c_dbl), ("beta", c_dbl), ("c", c_dbl),
+                ("switch_tol", c_dbl), ("f_target", c_dbl), ("max_newton", c_i32),
+                ("max_stage1", c_i32), ("max_cg", c_i32), ("ls_max", c_i32),
+                ("start_stage", c_i32), ("warm_start", c_i32), ("stall_iters", c_i32),
+                ("refresh_every", c_i32), ("profile", c_i32)]
+
+
+class tomo_fit_report(ctypes.Structure):
+    _fields_ = [("f", c_dbl), ("kkt", c_dbl), ("time_ms", c_dbl), ("iters_s1", c_i32),
+                ("iters_s2", c_i32), ("cg_total", c_i32), ("ls_total", c_i32),
+                ("refreshes", c_i32), ("stop", c_i32), ("stage_end", c_i32),
+                ("kernels", c_i32), ("fwd_count", c_i32), ("adj_count", c_i32),
+                ("fwd_ms", c_dbl), ("adj_ms", c_dbl)]
+
+
+# (name, restype, argtypes) of every entry point of include/tomo.h
+EXPORTS = [
+    ("tomo_plan", c_i32, [ctypes.POINTER(c_ptr), ctypes.POINTER(tomo_desc)]),
+    ("tomo_plan_destroy", None, [c_ptr]),
+    ("tomo_objective", c_i32, [c_ptr, c_ptr, c_ptr, ctypes.POINTER(c_dbl), c_ptr]),
+    ("tomo_fit_opts_default", None, [ctypes.POINTER(tomo_fit_opts)]),
+    ("tomo_fit", c_i32, [c_ptr, c_ptr, c_ptr, ctypes.POINTER(tomo_fit_opts),
+                         ctypes.POINTER(tomo_fit_report)]),
+    ("tomo_apply_F", c_i32, [c_ptr, c_ptr, c_ptr]),
+    ("tomo_apply_Ft", c_i32, [c_ptr, c_ptr, c_ptr]),
+    ("tomo_hvp", c_i32, [c_ptr, c_ptr, c_ptr]),
+    ("tomo_hess_diag", c_i32, [c_ptr, c_ptr]),
+    ("tomo_project_simplex", c_i32, [c_ptr, c_ptr, c_ptr]),
+    ("tomo_kkt", c_i32, [c_ptr, c_ptr, c_ptr, ctypes.POINTER(c_dbl)]),
+    ("tomo_poisson_weights", c_i32, [c_ptr, c_ptr, c_ptr, c_i64, c_ptr]),
+    ("tomo_bands", c_i32, [c_ptr, c_ptr, c_ptr]),
+    ("tomo_kernel_launches", c_i64, []),
+    ("tomo_last_error", ctypes.c_char_p, []),
+]
+
+_lib = None
+
+
+class TomoError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)}: {msg}")
+
+
+def lib(path: str | None = None) -> ctypes.CDLL:
+    """Loads libtomo.so (built by ``build.build()``); raises if it is missing."""
+    global _lib
+    if _lib is None:
+        p = path or _LIB_PATH
+        if not os.path.exists(p):
+            raise ImportError(f"libtomo.so not built ({p}); run paper_2404_02844_gb300.build.build()")
+        L = ctypes.CDLL(p)
+        for name, res, args in EXPORTS:
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(st: int, where: str, allow=(0,)):
+    if st not in allow:
+        raise TomoError(st, where, lib().tomo_last_error().decode())
+    return st
+
+
+# --------------------------------------------------------------- C-named API
+def tomo_plan(desc: tomo_desc) -> int:
+    h = c_ptr()
+    _check(lib().tomo_plan(ctypes.byref(h), ctypes.byref(desc)), "tomo_plan")
+    return h.value
+
+
+def tomo_plan_destroy(h: int) -> None:
+    lib().tomo_plan_destroy(h)
+
+
+def tomo_objective(h: int, P: int, Theta: int, grad: int | None = None) -> float:
+    f = c_dbl()
+    _check(lib().tomo_objective(h, P, Theta, ctypes.byref(f), grad), "tomo_objective")
+    return f.value
+
+
+def tomo_fit_opts_default() -> tomo_fit_opts:
+    o = tomo_fit_opts()
+    lib().tomo_fit_opts_default(ctypes.byref(o))
+    return o
+
+
+def tomo_fit(h: int, P: int, Theta: int, opts: tomo_fit_opts | None = None):
+    rep = tomo_fit_report()
+    st = lib().tomo_fit(h, P, Theta, ctypes.byref(opts) if opts is not None else None,
+                        ctypes.byref(rep))
+    _check(st, "tomo_fit", allow=(0, 4))
+    return st, rep
+
+
+def tomo_apply_F(h, X, O):
+    _check(lib().tomo_apply_F(h, X, O), "tomo_apply_F")
+
+
+def tomo_apply_Ft(h, Y, Z):
+    _check(lib().tomo_apply_Ft(h, Y, Z), "tomo_apply_Ft")
+
+
+def tomo_hvp(h, V, HV):
+    _check(lib().tomo_hvp(h, V, HV), "tomo_hvp")
+
+
+def tomo_hess_diag(h, out):
+    _check(lib().tomo_hess_diag(h, out), "tomo_hess_diag")
+
+
+def tomo_project_simplex(h, X, Y):
+    _check(lib().tomo_project_simplex(h, X, Y), "tomo_project_simplex")
+
+
+def tomo_kkt(h, Theta, G) -> float:
+    k = c_dbl()
+    _check(lib().tomo_kkt(h, Theta, G, ctypes.byref(k)), "tomo_kkt")
+    return k.value
+
+
+def tomo_poisson_weights(h, d, i, count, out):
+    _check(lib().tomo_poisson_weights(h, d, i, count, out), "tomo_poisson_weights")
+
+
+def tomo_bands(h, lo, hi):
+    _check(lib().tomo_bands(h, lo, hi), "tomo_bands")
+
+
+def tomo_kernel_launches() -> int:
+    return lib().tomo_kernel_launches()
+
+
+def tomo_last_error() -> str:
+    return lib().tomo_last_error().decode()
+
+
+# ------------------------------------------------------------------ wrapper
+def _ptr(a):
+    """Address of a torch tensor (device) or numpy array (host), float64 and
+    contiguous."""
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+            raise TypeError("numpy arrays must be float64 and C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        import torch
+        if a.dtype != torch.float64 or not a.is_contiguous():
+            raise TypeError("tensors must be float64 and contiguous")
+        return a.data_ptr()
+    raise TypeError(f"unsupported buffer type {type(a)}")
+
+
+def _fit_dict(rep: tomo_fit_report) -> dict:
+    d = {k: getattr(rep, k) for k, _ in tomo_fit_report._fields_}
+    d["stop_name"] = STOP.get(rep.stop, rep.stop)
+    return d
+
+
+class Plan:
+    """A planned problem: probes ``lam`` (sorted, >= 0), cutoff M, outcomes N,
+    Poisson band half-width ``band_k`` (<= 0: dense F), regularisation
+    ``gamma`` and contraction precision ('fp64' or 'fp32').
+
+    Work is ordered on torch's current CUDA stream at construction unless a
+    raw ``stream`` handle is given."""
+
+    def __init__(self, M, N, lam, band_k=10.0, gamma=0.0, precision="fp64", stream=None):
+        lam = np.ascontiguousarray(lam, dtype=np.float64)
+        self.M, self.N, self.D = int(M), int(N), int(lam.shape[0])
+        self.band_k, self.gamma = float(band_k), float(gamma)
+        self.precision = {"fp64": PREC_FP64, "fp32": PREC_FP32}[precision] \
+            if isinstance(precision, str) else int(precision)
+        if stream is None:
+            try:
+                import torch
+                if torch.cuda.is_available():
+                    stream = torch.cuda.current_stream().cuda_stream
+            except ImportError:
+                stream = None
+        self._lam = lam
+        desc = tomo_desc(self.M, self.N, self.D, lam.ctypes.data, self.band_k, self.gamma,
+                         self.precision, 0, stream or None, 0)
+        self._h = tomo_plan(desc)
+
+    @classmethod
+    def from_workload(cls, w, precision="fp64", **kw):
+        return cls(w.M, w.N, w.lam, w.band_k, w.gamma, precision=precision, **kw)
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h:
+            tomo_plan_destroy(h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ---------------------------------------------------------------- helpers
+    def _dev_empty(self, *shape):
+        import torch
+        return torch.empty(*shape, dtype=torch.float64, device="cuda")
+
+    def objective(self, P, Theta, want_grad=False):
+        G = None
+        if want_grad:
+            G = np.empty((self.M, self.N)) if isinstance(Theta, np.ndarray) \
+                else self._dev_empty(self.M, self.N)
+        f = tomo_objective(self._h, _ptr(P), _ptr(Theta), _ptr(G) if G is not None else None)
+        return (f, G) if want_grad else f
+
+    def fit(self, P, Theta=None, **opts):
+        """Algorithm 3.  Returns (Theta, report dict).  Theta (if given) is
+        the warm start and is overwritten with the result."""
+        o = tomo_fit_opts_default()
+        for k, v in opts.items():
+            if not hasattr(o, k):
+                raise KeyError(k)
+            setattr(o, k, v)
+        if Theta is None:
+            Theta = np.empty((self.M, self.N)) if isinstance(P, np.ndarray) \
+                else self._dev_empty(self.M, self.N)
+        else:
+            o.warm_start = 1 if "warm_start" not in opts else opts["warm_start"]
+        st, rep = tomo_fit(self._h, _ptr(P), _ptr(Theta), o)
+        d = _fit_dict(rep)
+        d["status"] = STATUS[st]
+        return Theta, d
+
+    def apply_F(self, X):
+        O = self._dev_empty(self.D, self.N)
+        tomo_apply_F(self._h, _ptr(X), _ptr(O))
+        return O
+
+    def apply_Ft(self, Y):
+        Z = self._dev_empty(self.M, self.N)
+        tomo_apply_Ft(self._h, _ptr(Y), _ptr(Z))
+        return Z
+
+    def hvp(self, V):
+        HV = self._dev_empty(self.M, self.N)
+        tomo_hvp(self._h, _ptr(V), _ptr(HV))
+        return HV
+
+    def hess_diag(self):
+        h = np.empty(self.M)
+        tomo_hess_diag(self._h, h.ctypes.data)
+        return h
+
+    def project_simplex(self, X):
+        Y = self._dev_empty(*tuple(X.shape))
+        tomo_project_simplex(self._h, _ptr(X), _ptr(Y))
+        return Y
+
+    def kkt(self, Theta, G):
+        return tomo_kkt(self._h, _ptr(Theta), _ptr(G))
+
+    def poisson_weights(self, d, i):
+        d = np.ascontiguousarray(d, dtype=np.int64)
+        i = np.ascontiguousarray(i, dtype=np.int64)
+        out = np.empty(d.shape[0])
+        tomo_poisson_weights(self._h, d.ctypes.data, i.ctypes.data, d.shape[0], out.ctypes.data)
+        return out
+
+    def bands(self):
+        lo = np.empty(self.D, np.int64)
+        hi = np.empty(self.D, np.int64)
+        tomo_bands(self._h, lo.ctypes.data, hi.ctypes.data)
+        return lo, hi

@@ -1,0 +1,622 @@
+// api.cu -- host side of libtomo: the C ABI declared in include/tomo.h.
+// Plans own every device table and workspace; tomo_fit drives the two-stage
+// two-metric projected truncated Newton method of App. B (Algorithm 3:
+// Algorithm 2 then Algorithm 1) with all vector work in the kernels of
+// band_gemm.cu / rowops.cu and only scalar decisions on the host.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdarg>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <utility>
+
+#include "tomo_internal.cuh"
+
+namespace tomo {
+
+static std::atomic<int64_t> g_launches{0};
+void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+static thread_local std::string g_err;
+
+static tomo_status fail(tomo_status s, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
+static tomo_status fail(tomo_status s, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+#define CUDA_TRY(expr)                                                                     \
+    do {                                                                                   \
+        cudaError_t _e = (expr);                                                           \
+        if (_e != cudaSuccess)                                                             \
+            return fail(_e == cudaErrorMemoryAllocation ? TOMO_ENOMEM : TOMO_ECUDA,        \
+                        "%s failed: %s (%s:%d)", #expr, cudaGetErrorString(_e), __FILE__,  \
+                        __LINE__);                                                         \
+    } while (0)
+
+#define TOMO_TRY(expr)                      \
+    do {                                    \
+        tomo_status _s = (expr);            \
+        if (_s != TOMO_OK) return _s;       \
+    } while (0)
+
+static bool is_device_pointer(const void *ptr)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+        cudaGetLastError();  // clear the sticky-free error of an unknown pointer
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+template <typename T>
+static cudaError_t dalloc(T **p, int64_t count)
+{
+    if (count < 1) count = 1;
+    return cudaMalloc(reinterpret_cast<void **>(p), sizeof(T) * size_t(count));
+}
+
+static void free_plan(Plan *p)
+{
+    if (!p) return;
+    void *dev[] = {p->lam, p->lo, p->hi, p->aoff, p->anchor, p->anchor_f, p->ratio_inv,
+                   p->ratio_inv_f, p->fwd_klo, p->fwd_khi, p->adj_dlo, p->adj_dhi, p->h,
+                   p->Th, p->trial, p->s, p->G, p->g, p->x, p->r, p->z, p->p, p->u, p->q,
+                   p->dir, p->R, p->Rt, p->O, p->Pbuf, p->Xbuf, p->freem, p->var, p->mrow,
+                   p->partials, p->sc, p->idx_buf, p->val_buf};
+    for (void *d : dev)
+        if (d) cudaFree(d);
+    if (p->sc_host) cudaFreeHost(p->sc_host);
+    if (p->scratch_host) cudaFreeHost(p->scratch_host);
+    if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
+    delete p;
+}
+
+static tomo_status read_scalars(Plan &p)
+{
+    CUDA_TRY(cudaMemcpyAsync(p.sc_host, p.sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, p.stream));
+    CUDA_TRY(cudaStreamSynchronize(p.stream));
+    return TOMO_OK;
+}
+
+// Stages a caller buffer of `count` doubles: device pointers are used as they
+// are, host buffers are copied into (lazily allocated) plan memory.
+static tomo_status stage_in(Plan &p, const double *src, int64_t count, double **buf,
+                            const double **out)
+{
+    if (is_device_pointer(src)) {
+        *out = src;
+        return TOMO_OK;
+    }
+    if (!*buf) CUDA_TRY(dalloc(buf, count));
+    CUDA_TRY(cudaMemcpyAsync(*buf, src, sizeof(double) * size_t(count), cudaMemcpyHostToDevice,
+                             p.stream));
+    *out = *buf;
+    return TOMO_OK;
+}
+
+static tomo_status check_finite(Plan &p, const double *x, int64_t n, const char *what)
+{
+    CUDA_TRY(launch_nonfinite_check(p, x, n, 0));
+    TOMO_TRY(read_scalars(p));
+    if (p.sc_host->nonfinite > 0.0)
+        return fail(TOMO_ENONFINITE, "%s holds %.0f non-finite values", what, p.sc_host->nonfinite);
+    return TOMO_OK;
+}
+
+// R = F Theta - P in double, f = ||R||^2 + g(Theta) (Eq. min + Eq. regul).
+static tomo_status residual_objective(Plan &p, const double *P, const double *Th, double *R,
+                                      double *f)
+{
+    CUDA_TRY(launch_forward(p, TOMO_PREC_FP64, FWD_RESID, Th, R, P, false));
+    CUDA_TRY(launch_regulariser(p, Th));
+    TOMO_TRY(read_scalars(p));
+    *f = p.sc_host->res2 + p.sc_host->regval;
+    return TOMO_OK;
+}
+
+}  // namespace tomo
+
+using namespace tomo;
+
+extern "C" {
+
+const char *tomo_last_error(void) { return g_err.c_str(); }
+
+int64_t tomo_kernel_launches(void) { return g_launches.load(); }
+
+void tomo_fit_opts_default(tomo_fit_opts *o)
+{
+    if (!o) return;
+    o->eps_kkt = 1e-10;
+    o->eps_bar = 1e-6;
+    o->beta = 0.75;
+    o->c = 0.1;
+    o->switch_tol = 1e-4;
+    o->f_target = 0.0;
+    o->max_newton = 1000;
+    o->max_stage1 = 200;
+    o->max_cg = 50;
+    o->ls_max = 50;
+    o->start_stage = 1;
+    o->warm_start = 0;
+    o->stall_iters = 5;
+    o->refresh_every = 8;
+    o->profile = 0;
+}
+
+tomo_status tomo_plan(tomo_plan_t *out, const tomo_desc *d)
+{
+    if (!out) return fail(TOMO_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!d) return fail(TOMO_EINVAL, "desc is NULL");
+    if (d->M < 1 || d->M > (int64_t(1) << 30)) return fail(TOMO_EINVAL, "M=%lld out of range", (long long)d->M);
+    if (d->N < 2 || d->N > MAX_N) return fail(TOMO_EINVAL, "N=%lld out of range [2, %d]", (long long)d->N, MAX_N);
+    if (d->D < 1 || d->D > (int64_t(1) << 30)) return fail(TOMO_EINVAL, "D=%lld out of range", (long long)d->D);
+    if (!d->lambda) return fail(TOMO_EINVAL, "lambda is NULL");
+    if (!std::isfinite(d->gamma) || d->gamma < 0.0) return fail(TOMO_EINVAL, "gamma must be finite and >= 0");
+    if (!std::isfinite(d->band_k)) return fail(TOMO_EINVAL, "band_k must be finite");
+    if (d->precision != TOMO_PREC_FP64 && d->precision != TOMO_PREC_FP32)
+        return fail(TOMO_EINVAL, "unknown precision %d", d->precision);
+    if (d->flags != 0) return fail(TOMO_EINVAL, "flags must be 0");
+    for (int64_t k = 0; k < d->D; ++k) {
+        const double l = d->lambda[k];
+        if (!std::isfinite(l) || l < 0.0) return fail(TOMO_EINVAL, "lambda[%lld] is not finite and >= 0", (long long)k);
+        if (k > 0 && l < d->lambda[k - 1])
+            return fail(TOMO_EINVAL, "lambda must be non-decreasing (lambda[%lld] < lambda[%lld])",
+                        (long long)k, (long long)(k - 1));
+    }
+    if ((d->M * d->N) > (int64_t(1) << 40) || (d->D * d->N) > (int64_t(1) << 40))
+        return fail(TOMO_EINVAL, "problem too large");
+
+    Plan *p = new (std::nothrow) Plan();
+    if (!p) return fail(TOMO_ENOMEM, "host allocation failed");
+    std::memset(p, 0, sizeof(Plan));
+    p->M = d->M; p->N = d->N; p->D = d->D;
+    p->gamma = d->gamma; p->band_k = d->band_k; p->precision = d->precision;
+
+    auto bail = [&](tomo_status s) { free_plan(p); return s; };
+#define PLAN_TRY(expr)                                                                     \
+    do {                                                                                   \
+        cudaError_t _e = (expr);                                                           \
+        if (_e != cudaSuccess)                                                             \
+            return bail(fail(_e == cudaErrorMemoryAllocation ? TOMO_ENOMEM : TOMO_ECUDA,    \
+                             "%s failed: %s", #expr, cudaGetErrorString(_e)));             \
+    } while (0)
+
+    PLAN_TRY(cudaGetDevice(&p->device));
+    PLAN_TRY(cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device));
+    if (d->stream) {
+        p->stream = static_cast<cudaStream_t>(d->stream);
+    } else {
+        PLAN_TRY(cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking));
+        p->own_stream = true;
+    }
+    const int64_t M = p->M, N = p->N, D = p->D, MN = M * N, DN = D * N;
+    p->fwd_tiles = int((D + FWD_BD - 1) / FWD_BD);
+    p->adj_tiles = int((M + ADJ_BI - 1) / ADJ_BI);
+    const int64_t ncol32 = (N + 31) / 32;
+    int64_t mp = int64_t(p->num_sms) * 8;
+    if (int64_t(p->fwd_tiles) * ncol32 > mp) mp = int64_t(p->fwd_tiles) * ncol32;
+    if (int64_t(p->adj_tiles) * ncol32 > mp) mp = int64_t(p->adj_tiles) * ncol32;
+    p->max_partials = mp;
+
+    PLAN_TRY(dalloc(&p->lam, D));
+    PLAN_TRY(dalloc(&p->lo, D));
+    PLAN_TRY(dalloc(&p->hi, D));
+    PLAN_TRY(dalloc(&p->aoff, D + 1));
+    PLAN_TRY(dalloc(&p->ratio_inv, M + RUN + 1));
+    PLAN_TRY(dalloc(&p->ratio_inv_f, M + RUN + 1));
+    PLAN_TRY(dalloc(&p->fwd_klo, p->fwd_tiles));
+    PLAN_TRY(dalloc(&p->fwd_khi, p->fwd_tiles));
+    PLAN_TRY(dalloc(&p->adj_dlo, p->adj_tiles));
+    PLAN_TRY(dalloc(&p->adj_dhi, p->adj_tiles));
+    PLAN_TRY(dalloc(&p->h, M));
+    double **mn_bufs[] = {&p->Th, &p->trial, &p->s, &p->G, &p->g, &p->x, &p->r,
+                          &p->z, &p->p, &p->u, &p->q, &p->dir};
+    for (double **b : mn_bufs) PLAN_TRY(dalloc(b, MN));
+    PLAN_TRY(dalloc(&p->R, DN));
+    PLAN_TRY(dalloc(&p->Rt, DN));
+    PLAN_TRY(dalloc(&p->O, DN));
+    PLAN_TRY(dalloc(&p->freem, MN));
+    PLAN_TRY(dalloc(&p->var, MN));
+    PLAN_TRY(dalloc(&p->mrow, M));
+    PLAN_TRY(dalloc(&p->partials, RED_SLOTS * p->max_partials));
+    PLAN_TRY(dalloc(&p->sc, 1));
+    PLAN_TRY(cudaMallocHost(reinterpret_cast<void **>(&p->sc_host), sizeof(DevScalars)));
+    PLAN_TRY(cudaMallocHost(reinterpret_cast<void **>(&p->scratch_host), 64 * sizeof(double)));
+    PLAN_TRY(cudaMemsetAsync(p->sc, 0, sizeof(DevScalars), p->stream));
+    PLAN_TRY(cudaMemcpyAsync(p->lam, d->lambda, sizeof(double) * size_t(D), cudaMemcpyHostToDevice,
+                             p->stream));
+    PLAN_TRY(launch_plan_tables(*p));
+    PLAN_TRY(launch_hess_diag(*p));
+    PLAN_TRY(cudaStreamSynchronize(p->stream));
+#undef PLAN_TRY
+    *out = reinterpret_cast<tomo_plan_t>(p);
+    return TOMO_OK;
+}
+
+void tomo_plan_destroy(tomo_plan_t plan)
+{
+    Plan *p = reinterpret_cast<Plan *>(plan);
+    if (!p) return;
+    cudaStreamSynchronize(p->stream);
+    free_plan(p);
+}
+
+tomo_status tomo_objective(tomo_plan_t plan, const double *P, const double *Theta, double *f_host,
+                           double *grad)
+{
+    Plan *pp = reinterpret_cast<Plan *>(plan);
+    if (!pp || !P || !Theta || !f_host) return fail(TOMO_EINVAL, "NULL argument");
+    Plan &p = *pp;
+    const int64_t MN = p.M * p.N, DN = p.D * p.N;
+    const double *Pd, *Td;
+    TOMO_TRY(stage_in(p, P, DN, &p.Pbuf, &Pd));
+    TOMO_TRY(stage_in(p, Theta, MN, &p.Xbuf, &Td));
+    TOMO_TRY(check_finite(p, Pd, DN, "P"));
+    TOMO_TRY(check_finite(p, Td, MN, "Theta"));
+    double f = 0.0;
+    TOMO_TRY(residual_objective(p, Pd, Td, p.R, &f));
+    *f_host = f;
+    if (grad) {
+        const bool gdev = is_device_pointer(grad);
+        double *gd = gdev ? grad : p.G;
+        CUDA_TRY(launch_adjoint(p, p.precision, ADJ_GRAD, p.R, gd, Td, false));
+        if (!gdev)
+            CUDA_TRY(cudaMemcpyAsync(grad, gd, sizeof(double) * size_t(MN), cudaMemcpyDeviceToHost,
+                                     p.stream));
+    }
+    CUDA_TRY(cudaStreamSynchronize(p.stream));
+    if (!std::isfinite(f)) return fail(TOMO_ENONFINITE, "objective is not finite");
+    return TOMO_OK;
+}
+
+}  // extern "C"
+
+namespace tomo {
+
+// Hessian products of the CG loop, launched `count` times; every kernel is
+// gated on the device flag cg_active, so launches after convergence are
+// empty.  Stage 1 multiplies p itself, stage 2 the lifted u = E p.
+constexpr int CG_CHUNK = 4;
+
+// Events bracketing the band contractions of one CG chunk (profiling).
+struct ChunkEvents {
+    cudaEvent_t ev[CG_CHUNK][3];
+    bool ready = false;
+    tomo_status init()
+    {
+        if (ready) return TOMO_OK;
+        for (auto &row : ev)
+            for (auto &e : row) CUDA_TRY(cudaEventCreate(&e));
+        ready = true;
+        return TOMO_OK;
+    }
+    ~ChunkEvents()
+    {
+        if (!ready) return;
+        for (auto &row : ev)
+            for (auto &e : row) cudaEventDestroy(e);
+    }
+};
+
+static tomo_status cg_chunk(Plan &p, int stage, int count, ChunkEvents *evs)
+{
+    const double *in = stage == 1 ? p.p : p.u;
+    for (int c = 0; c < count; ++c) {
+        if (evs) CUDA_TRY(cudaEventRecord(evs->ev[c][0], p.stream));
+        CUDA_TRY(launch_forward(p, p.precision, FWD_STORE, in, p.O, nullptr, true));
+        if (evs) CUDA_TRY(cudaEventRecord(evs->ev[c][1], p.stream));
+        CUDA_TRY(launch_adjoint(p, p.precision, ADJ_HESS, p.O, p.q, in, true));
+        if (evs) CUDA_TRY(cudaEventRecord(evs->ev[c][2], p.stream));
+        CUDA_TRY(launch_cg_restrict(p, stage));
+        CUDA_TRY(launch_cg_update_xr(p, stage));
+        CUDA_TRY(launch_cg_update_p(p, stage));
+    }
+    return TOMO_OK;
+}
+
+struct LsResult {
+    bool ok;
+    double f_new, gts, alpha;
+};
+
+// Backtracking line search of App. B along dir (or -g/diag when the device
+// flag use_grad_dir is set): alpha = beta^m, m = 0, 1, ...; accept the first
+// trial with f(trial) <= f + c g^T (trial - Theta) (stage 2 also needs every
+// implicit entry Theta_{i,m(i)} >= 0).  Direct mode evaluates f(trial) from a
+// fresh residual F trial - P; delta mode from R + F s with s = trial - Theta.
+static tomo_status line_search(Plan &p, int stage, const double *P, double f,
+                               const tomo_fit_opts &o, bool delta, int32_t *ls_count, LsResult *res)
+{
+    res->ok = false;
+    double alpha = 1.0;
+    for (int m = 0; m < o.ls_max; ++m, alpha *= o.beta) {
+        ++*ls_count;
+        CUDA_TRY(launch_trial(p, stage, alpha, delta));
+        if (delta)
+            CUDA_TRY(launch_forward_gated_ls(p, p.precision, FWD_DELTA, p.s, p.Rt, p.R));
+        else
+            CUDA_TRY(launch_forward_gated_ls(p, TOMO_PREC_FP64, FWD_RESID, p.trial, p.Rt, P));
+        TOMO_TRY(read_scalars(p));
+        const DevScalars &s = *p.sc_host;
+        if (s.neg) continue;
+        bool accept;
+        double fn;
+        if (delta) {
+            const double df = s.dres + s.reg;
+            accept = df <= o.c * s.gts;
+            fn = f + df;
+        } else {
+            fn = s.res2 + s.reg;
+            accept = fn <= f + o.c * s.gts;
+        }
+        if (accept) {
+            res->ok = true;
+            res->f_new = fn;
+            res->gts = s.gts;
+            res->alpha = alpha;
+            return TOMO_OK;
+        }
+    }
+    return TOMO_OK;
+}
+
+static tomo_status fit_impl(Plan &p, const double *P, const tomo_fit_opts &o, tomo_fit_report &rep)
+{
+    const int64_t M = p.M, N = p.N;
+    const double MN = double(M) * double(N);
+    const bool fp64 = p.precision == TOMO_PREC_FP64;
+    const bool delta = !fp64;
+    ChunkEvents evs;
+    if (o.profile) TOMO_TRY(evs.init());
+    double f = 0.0;
+    TOMO_TRY(residual_objective(p, P, p.Th, p.R, &f));
+    rep.refreshes = 1;
+    int stage = o.start_stage == 2 ? 2 : 1;
+    int stall = 0, since_refresh = 0;
+    rep.stop = 2;
+    for (int k = 0; k < o.max_newton; ++k) {
+        // gradient G = 2 F^T R + 2 gamma L Theta
+        CUDA_TRY(launch_adjoint(p, p.precision, ADJ_GRAD, p.R, p.G, p.Th, false));
+        if (stage == 1 && rep.iters_s1 >= o.max_stage1) stage = 2;
+        CUDA_TRY(launch_setup1(p, stage, o.eps_bar));
+        CUDA_TRY(launch_setup2(p, stage, o.max_cg));
+        TOMO_TRY(read_scalars(p));
+        const double kkt = std::sqrt(p.sc_host->kkt2 / MN);
+        if (!std::isfinite(kkt) || !std::isfinite(f))
+            return fail(TOMO_ENONFINITE, "non-finite objective or gradient at iteration %d", k);
+        if (kkt <= o.eps_kkt) { rep.stop = 0; break; }
+        if (o.f_target > 0.0 && f <= o.f_target) {
+            if (!fp64 && since_refresh > 0) {
+                TOMO_TRY(residual_objective(p, P, p.Th, p.R, &f));
+                ++rep.refreshes;
+                since_refresh = 0;
+            }
+            if (f <= o.f_target) { rep.stop = 1; break; }
+        }
+        // truncated Newton direction: PCG on the free variables
+        int active = p.sc_host->cg_active;
+        int done = 0;
+        while (active) {
+            TOMO_TRY(cg_chunk(p, stage, CG_CHUNK, o.profile ? &evs : nullptr));
+            TOMO_TRY(read_scalars(p));
+            active = p.sc_host->cg_active;
+            if (o.profile) {
+                // only the iterations that ran (the rest of the chunk exited
+                // at the gate) are counted
+                const int ran = p.sc_host->cg_iters - done;
+                for (int c = 0; c < ran && c < CG_CHUNK; ++c) {
+                    float a = 0.f, b = 0.f;
+                    CUDA_TRY(cudaEventElapsedTime(&a, evs.ev[c][0], evs.ev[c][1]));
+                    CUDA_TRY(cudaEventElapsedTime(&b, evs.ev[c][1], evs.ev[c][2]));
+                    rep.fwd_ms += a;
+                    rep.adj_ms += b;
+                    ++rep.fwd_count;
+                    ++rep.adj_count;
+                }
+            }
+            done = p.sc_host->cg_iters;
+        }
+        rep.cg_total += p.sc_host->cg_iters;
+        CUDA_TRY(launch_direction(p, stage));
+        if (stage == 1) ++rep.iters_s1; else ++rep.iters_s2;
+
+        LsResult ls;
+        TOMO_TRY(line_search(p, stage, P, f, o, delta, &rep.ls_total, &ls));
+        if (!ls.ok) {
+            CUDA_TRY(launch_set_grad_dir(p));
+            TOMO_TRY(line_search(p, stage, P, f, o, delta, &rep.ls_total, &ls));
+        }
+        if (!ls.ok) {
+            if (stage == 1) { stage = 2; continue; }
+            rep.stop = 3;
+            break;
+        }
+        std::swap(p.Th, p.trial);
+        std::swap(p.R, p.Rt);
+        if (stage == 1 && std::fabs(ls.gts / ls.alpha) <= o.switch_tol) stage = 2;
+        const double f_new = ls.f_new;
+        if (!(f_new < f * (1.0 - 1e-15))) {
+            if (++stall >= o.stall_iters) { f = f_new; rep.stop = 3; break; }
+        } else {
+            stall = 0;
+        }
+        f = f_new;
+        if (!fp64 && ++since_refresh >= o.refresh_every) {
+            TOMO_TRY(residual_objective(p, P, p.Th, p.R, &f));
+            ++rep.refreshes;
+            since_refresh = 0;
+        }
+    }
+    // final state, always in double
+    TOMO_TRY(residual_objective(p, P, p.Th, p.R, &f));
+    CUDA_TRY(launch_adjoint(p, TOMO_PREC_FP64, ADJ_GRAD, p.R, p.G, p.Th, false));
+    CUDA_TRY(launch_kkt(p, p.Th, p.G));
+    TOMO_TRY(read_scalars(p));
+    rep.f = f;
+    rep.kkt = std::sqrt(p.sc_host->kkt2 / MN);
+    rep.stage_end = stage;
+    if (!std::isfinite(f)) return fail(TOMO_ENONFINITE, "objective is not finite");
+    return TOMO_OK;
+}
+
+}  // namespace tomo
+
+extern "C" {
+
+tomo_status tomo_fit(tomo_plan_t plan, const double *P, double *Theta, const tomo_fit_opts *opts,
+                     tomo_fit_report *report)
+{
+    Plan *pp = reinterpret_cast<Plan *>(plan);
+    if (!pp || !P || !Theta) return fail(TOMO_EINVAL, "NULL argument");
+    Plan &p = *pp;
+    tomo_fit_opts o;
+    if (opts) o = *opts; else tomo_fit_opts_default(&o);
+    if (!(o.beta > 0.0 && o.beta < 1.0) || !(o.c > 0.0 && o.c < 1.0) || o.max_newton < 0 ||
+        o.max_cg < 0 || o.ls_max < 1 || !(o.eps_bar >= 0.0) || !(o.eps_kkt >= 0.0) ||
+        o.refresh_every < 1 || o.stall_iters < 1)
+        return fail(TOMO_EINVAL, "invalid options");
+    tomo_fit_report rep;
+    std::memset(&rep, 0, sizeof(rep));
+    const int64_t l0 = tomo_kernel_launches();
+    const auto t0 = std::chrono::steady_clock::now();
+    const int64_t MN = p.M * p.N, DN = p.D * p.N;
+    const double *Pd;
+    TOMO_TRY(stage_in(p, P, DN, &p.Pbuf, &Pd));
+    TOMO_TRY(check_finite(p, Pd, DN, "P"));
+    const bool tdev = is_device_pointer(Theta);
+    if (o.warm_start) {
+        CUDA_TRY(cudaMemcpyAsync(p.Th, Theta, sizeof(double) * size_t(MN),
+                                 tdev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, p.stream));
+        TOMO_TRY(check_finite(p, p.Th, MN, "Theta"));
+    } else {
+        CUDA_TRY(launch_fill(p, p.Th, 1.0 / double(p.N), MN));
+    }
+    tomo_status st = fit_impl(p, Pd, o, rep);
+    if (st != TOMO_OK) return st;
+    CUDA_TRY(cudaMemcpyAsync(Theta, p.Th, sizeof(double) * size_t(MN),
+                             tdev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, p.stream));
+    CUDA_TRY(cudaStreamSynchronize(p.stream));
+    rep.time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    rep.kernels = int32_t(tomo_kernel_launches() - l0);
+    if (report) *report = rep;
+    return rep.stop == 2 ? TOMO_ENOTCONV : TOMO_OK;
+}
+
+tomo_status tomo_apply_F(tomo_plan_t plan, const double *X, double *O)
+{
+    Plan *p = reinterpret_cast<Plan *>(plan);
+    if (!p || !X || !O) return fail(TOMO_EINVAL, "NULL argument");
+    CUDA_TRY(launch_forward(*p, p->precision, FWD_STORE, X, O, nullptr, false));
+    CUDA_TRY(cudaStreamSynchronize(p->stream));
+    return TOMO_OK;
+}
+
+tomo_status tomo_apply_Ft(tomo_plan_t plan, const double *Y, double *Z)
+{
+    Plan *p = reinterpret_cast<Plan *>(plan);
+    if (!p || !Y || !Z) return fail(TOMO_EINVAL, "NULL argument");
+    CUDA_TRY(launch_adjoint(*p, p->precision, ADJ_STORE, Y, Z, nullptr, false));
+    CUDA_TRY(cudaStreamSynchronize(p->stream));
+    return TOMO_OK;
+}
+
+tomo_status tomo_hvp(tomo_plan_t plan, const double *V, double *HV)
+{
+    Plan *p = reinterpret_cast<Plan *>(plan);
+    if (!p || !V || !HV) return fail(TOMO_EINVAL, "NULL argument");
+    CUDA_TRY(launch_forward(*p, p->precision, FWD_STORE, V, p->O, nullptr, false));
+    CUDA_TRY(launch_adjoint(*p, p->precision, ADJ_GRAD, p->O, HV, V, false));
+    CUDA_TRY(cudaStreamSynchronize(p->stream));
+    return TOMO_OK;
+}
+
+tomo_status tomo_hess_diag(tomo_plan_t plan, double *h)
+{
+    Plan *p = reinterpret_cast<Plan *>(plan);
+    if (!p || !h) return fail(TOMO_EINVAL, "NULL argument");
+    CUDA_TRY(cudaMemcpyAsync(h, p->h, sizeof(double) * size_t(p->M), cudaMemcpyDefault, p->stream));
+    CUDA_TRY(cudaStreamSynchronize(p->stream));
+    return TOMO_OK;
+}
+
+tomo_status tomo_project_simplex(tomo_plan_t plan, const double *X, double *Y)
+{
+    Plan *p = reinterpret_cast<Plan *>(plan);
+    if (!p || !X || !Y) return fail(TOMO_EINVAL, "NULL argument");
+    CUDA_TRY(launch_project_rows(*p, X, Y));
+    CUDA_TRY(cudaStreamSynchronize(p->stream));
+    return TOMO_OK;
+}
+
+tomo_status tomo_kkt(tomo_plan_t plan, const double *Theta, const double *G, double *kkt_host)
+{
+    Plan *p = reinterpret_cast<Plan *>(plan);
+    if (!p || !Theta || !G || !kkt_host) return fail(TOMO_EINVAL, "NULL argument");
+    CUDA_TRY(launch_kkt(*p, Theta, G));
+    TOMO_TRY(read_scalars(*p));
+    *kkt_host = std::sqrt(p->sc_host->kkt2 / (double(p->M) * double(p->N)));
+    return TOMO_OK;
+}
+
+tomo_status tomo_poisson_weights(tomo_plan_t plan, const int64_t *d, const int64_t *i,
+                                 int64_t count, double *out_host)
+{
+    Plan *p = reinterpret_cast<Plan *>(plan);
+    if (!p || (count > 0 && (!d || !i || !out_host)) || count < 0)
+        return fail(TOMO_EINVAL, "invalid argument");
+    if (count == 0) return TOMO_OK;
+    if (count > p->idx_cap) {
+        if (p->idx_buf) cudaFree(p->idx_buf);
+        if (p->val_buf) cudaFree(p->val_buf);
+        p->idx_buf = nullptr;
+        p->val_buf = nullptr;
+        p->idx_cap = 0;
+        CUDA_TRY(dalloc(&p->idx_buf, 2 * count));
+        CUDA_TRY(dalloc(&p->val_buf, count));
+        p->idx_cap = count;
+    }
+    CUDA_TRY(cudaMemcpyAsync(p->idx_buf, d, sizeof(int64_t) * size_t(count), cudaMemcpyHostToDevice, p->stream));
+    CUDA_TRY(cudaMemcpyAsync(p->idx_buf + count, i, sizeof(int64_t) * size_t(count), cudaMemcpyHostToDevice, p->stream));
+    CUDA_TRY(launch_poisson_weights(*p, p->idx_buf, p->idx_buf + count, count, p->val_buf));
+    CUDA_TRY(cudaMemcpyAsync(out_host, p->val_buf, sizeof(double) * size_t(count), cudaMemcpyDeviceToHost, p->stream));
+    CUDA_TRY(cudaStreamSynchronize(p->stream));
+    return TOMO_OK;
+}
+
+tomo_status tomo_bands(tomo_plan_t plan, int64_t *lo_host, int64_t *hi_host)
+{
+    Plan *p = reinterpret_cast<Plan *>(plan);
+    if (!p || !lo_host || !hi_host) return fail(TOMO_EINVAL, "NULL argument");
+    int32_t *tmp = new (std::nothrow) int32_t[size_t(2 * p->D)];
+    if (!tmp) return fail(TOMO_ENOMEM, "host allocation failed");
+    cudaError_t e1 = cudaMemcpyAsync(tmp, p->lo, sizeof(int32_t) * size_t(p->D), cudaMemcpyDeviceToHost, p->stream);
+    cudaError_t e2 = cudaMemcpyAsync(tmp + p->D, p->hi, sizeof(int32_t) * size_t(p->D), cudaMemcpyDeviceToHost, p->stream);
+    cudaError_t e3 = cudaStreamSynchronize(p->stream);
+    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+        delete[] tmp;
+        return fail(TOMO_ECUDA, "copy of the bands failed");
+    }
+    for (int64_t k = 0; k < p->D; ++k) {
+        lo_host[k] = tmp[k];
+        hi_host[k] = tmp[p->D + k];
+    }
+    delete[] tmp;
+    return TOMO_OK;
+}
+
+}  // extern "C"

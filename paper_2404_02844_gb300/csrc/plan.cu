@@ -1,0 +1,303 @@
+// plan.cu -- plan-time tables of the band contractions, built on the device:
+//   * band of every probe (the truncation of F, Sec. Data distribution: F is
+//     sparse and banded for large M),
+//   * Poisson anchors F_{d,i} at every RUN-th photon number of each band
+//     (Eq. Fmatrix) evaluated in log space in double,
+//   * per-tile photon-number / probe ranges of the forward and adjoint tiles,
+//   * the Hessian diagonal h_i = 2 sum_d F_{d,i}^2 + 2 gamma L_ii (Table ops).
+//
+// Log-space Poisson weights use the saddle-point form of C. Loader, "Fast and
+// accurate computation of binomial probabilities" (2000):
+//     ln p(i; lambda) = -1/2 ln(2 pi i) - stirlerr(i) - bd0(i, lambda),   i >= 1,
+// with stirlerr(n) = ln n! - (n + 1/2) ln n + n - 1/2 ln(2 pi) (the error of
+// Stirling's formula) and bd0(x, m) = x ln(x/m) + m - x, both evaluated
+// without the cancellation of the naive i ln(lambda) - lambda - ln i!, whose
+// terms reach 1e7 at i ~ 1e6.
+#include <cub/device/device_scan.cuh>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "tomo_device.cuh"
+#include "tomo_internal.cuh"
+
+namespace tomo {
+
+// stirlerr(n) for integer n >= 1.  n <= 15: from ln n! of the exactly
+// representable integer n!; n > 15: the asymptotic series of ln Gamma with
+// the Bernoulli coefficients B_2k / (2k (2k-1)) = 1/12, -1/360, 1/1260,
+// -1/1680, 1/1188 (next term < 2e-16 relative at n = 16).
+__device__ double stirlerr(double n)
+{
+    const double half_ln_2pi = 0.91893853320467274178;  // ln(2 pi) / 2
+    if (n <= 15.0) {
+        double fact = 1.0;
+        for (int k = 2; k <= int(n); ++k) fact *= double(k);
+        return log(fact) - (n + 0.5) * log(n) + n - half_ln_2pi;
+    }
+    const double nn = n * n;
+    const double S0 = 1.0 / 12.0, S1 = 1.0 / 360.0, S2 = 1.0 / 1260.0,
+                 S3 = 1.0 / 1680.0, S4 = 1.0 / 1188.0;
+    return (S0 - (S1 - (S2 - (S3 - S4 / nn) / nn) / nn) / nn) / n;
+}
+
+// bd0(x, m) = x ln(x/m) + m - x.  Near x = m it is summed from
+// v = (x-m)/(x+m):  ln(x/m) = 2 atanh(v), hence
+//     bd0 = v (x - m) + 2 x sum_{j>=1} v^(2j+1) / (2j+1).
+__device__ double bd0(double x, double m)
+{
+    if (fabs(x - m) < 0.1 * (x + m)) {
+        const double v = (x - m) / (x + m);
+        const double v2 = v * v;
+        double s = (x - m) * v;
+        double ej = 2.0 * x * v;
+        for (int j = 1; j < 200; ++j) {
+            ej *= v2;
+            const double s1 = s + ej / double(2 * j + 1);
+            if (s1 == s) return s1;
+            s = s1;
+        }
+        return s;
+    }
+    return x * log(x / m) + m - x;
+}
+
+// ln F_{d,i} for lambda > 0 (Eq. Fmatrix in log space).
+__device__ double log_poisson(double i, double lam)
+{
+    if (i == 0.0) return -lam;
+    const double ln_2pi = 1.83787706640934548356;
+    return -0.5 * (ln_2pi + log(i)) - stirlerr(i) - bd0(i, lam);
+}
+
+__device__ double poisson_weight(int64_t i, double lam)
+{
+    if (lam == 0.0) return i == 0 ? 1.0 : 0.0;
+    return exp(log_poisson(double(i), lam));
+}
+
+// Band of probe d.  The products and differences are rounded explicitly
+// (no fused multiply-add) so that the integer bounds are those of the plain
+// IEEE evaluation round(lambda - round(k sqrt(lambda))).
+__global__ void k_bands(int64_t D, int64_t M, double band_k, const double *lam,
+                        int32_t *lo, int32_t *hi, int64_t *cnt)
+{
+    const int64_t d = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (d >= D) return;
+    int64_t l, h;
+    if (band_k <= 0.0) {
+        l = 0;
+        h = M - 1;
+    } else {
+        const double x = lam[d];
+        const double s = sqrt(x);
+        const double ks = __dmul_rn(band_k, s);
+        const double a = floor(__dsub_rn(x, ks));
+        double b = ceil(__dadd_rn(x, ks));
+        if (b < 16.0) b = 16.0;
+        l = a < 0.0 ? 0 : int64_t(a);
+        h = b > double(M - 1) ? M - 1 : int64_t(b);
+        if (l > M - 1) l = M;
+    }
+    lo[d] = int32_t(l);
+    hi[d] = int32_t(h);
+    const int64_t a0 = l & ~int64_t(RUN - 1);
+    cnt[d] = (l <= h) ? (h - a0) / RUN + 1 : 0;
+}
+
+__global__ void k_anchors(int64_t D, const double *lam, const int32_t *lo, const int32_t *hi,
+                          const int64_t *aoff, double *anc, float *anc_f)
+{
+    const int64_t d = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (d >= D) return;
+    const int64_t l = lo[d], h = hi[d];
+    if (l > h) return;
+    const int64_t a0 = l & ~int64_t(RUN - 1);
+    const double x = lam[d];
+    int64_t k = aoff[d];
+    for (int64_t i = a0; i <= h; i += RUN, ++k) {
+        const double v = poisson_weight(i, x);
+        anc[k] = v;
+        anc_f[k] = float(v);
+    }
+}
+
+__global__ void k_ratio_inv(int64_t n, double *r, float *rf)
+{
+    const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (i >= n) return;
+    const double v = i == 0 ? 0.0 : 1.0 / double(i);
+    r[i] = v;
+    rf[i] = float(v);
+}
+
+// Forward tile t covers probes [FWD_BD t, FWD_BD (t+1)): union of their bands.
+__global__ void k_fwd_tiles(int64_t D, int tiles, const int32_t *lo, const int32_t *hi,
+                            int32_t *klo, int32_t *khi)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= tiles) return;
+    int32_t a = INT32_MAX, b = -1;
+    for (int64_t d = int64_t(t) * FWD_BD; d < D && d < int64_t(t + 1) * FWD_BD; ++d) {
+        if (lo[d] > hi[d]) continue;
+        a = min(a, lo[d]);
+        b = max(b, hi[d]);
+    }
+    if (b < 0) { a = 1; b = 0; }
+    klo[t] = a;
+    khi[t] = b;
+}
+
+// Adjoint tile t covers photon numbers [ADJ_BI t, ADJ_BI (t+1)).  With probes
+// sorted by intensity, lo_d and hi_d are non-decreasing in d, so the probes
+// whose band meets the tile form the range [first d with hi_d >= i0,
+// last d with lo_d <= i1] (binary searches).
+__global__ void k_adj_tiles(int64_t D, int64_t M, int tiles, const int32_t *lo,
+                            const int32_t *hi, int32_t *dlo, int32_t *dhi)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= tiles) return;
+    const int64_t i0 = int64_t(t) * ADJ_BI;
+    int64_t i1 = i0 + ADJ_BI - 1;
+    if (i1 > M - 1) i1 = M - 1;
+    int64_t a = 0, b = D;  // first d with hi_d >= i0
+    while (a < b) {
+        const int64_t mid = (a + b) / 2;
+        if (hi[mid] >= i0) b = mid; else a = mid + 1;
+    }
+    const int64_t first = a;
+    a = 0; b = D;          // first d with lo_d > i1
+    while (a < b) {
+        const int64_t mid = (a + b) / 2;
+        if (lo[mid] > i1) b = mid; else a = mid + 1;
+    }
+    const int64_t last = a - 1;
+    dlo[t] = int32_t(first);
+    dhi[t] = int32_t(last);
+}
+
+// F_{d,i} expanded from its anchor exactly as the contraction kernels do
+// (double version).
+__device__ double weight_from_anchor_d(int64_t d, int64_t i, const double *lam,
+                                       const int32_t *lo, const int32_t *hi,
+                                       const int64_t *aoff, const double *anc,
+                                       const double *rinv)
+{
+    if (i < lo[d] || i > hi[d]) return 0.0;
+    const int64_t a0 = int64_t(lo[d]) & ~int64_t(RUN - 1);
+    const int64_t ir = i & ~int64_t(RUN - 1);
+    double v = anc[aoff[d] + (ir - a0) / RUN];
+    const double x = lam[d];
+    for (int64_t j = ir; j < i; ++j) v = v * (x * rinv[j + 1]);
+    return v;
+}
+
+__device__ float weight_from_anchor_f(int64_t d, int64_t i, const double *lam,
+                                      const int32_t *lo, const int32_t *hi,
+                                      const int64_t *aoff, const float *anc,
+                                      const float *rinv)
+{
+    if (i < lo[d] || i > hi[d]) return 0.0f;
+    const int64_t a0 = int64_t(lo[d]) & ~int64_t(RUN - 1);
+    const int64_t ir = i & ~int64_t(RUN - 1);
+    float v = anc[aoff[d] + (ir - a0) / RUN];
+    const float x = float(lam[d]);
+    for (int64_t j = ir; j < i; ++j) v = v * (x * rinv[j + 1]);
+    return v;
+}
+
+// h_i = 2 sum_d F_{d,i}^2 + 2 gamma L_ii, one thread per photon number,
+// probes in increasing order (deterministic).
+__global__ void k_hess_diag(int64_t M, double gamma, const double *lam, const int32_t *lo,
+                            const int32_t *hi, const int64_t *aoff, const double *anc,
+                            const double *rinv, const int32_t *dlo, const int32_t *dhi,
+                            double *h)
+{
+    const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (i >= M) return;
+    const int t = int(i / ADJ_BI);
+    double s = 0.0;
+    for (int64_t d = dlo[t]; d <= dhi[t]; ++d) {
+        const double f = weight_from_anchor_d(d, i, lam, lo, hi, aoff, anc, rinv);
+        s += f * f;
+    }
+    const double lii = double((i > 0) + (i < M - 1));
+    h[i] = 2.0 * s + 2.0 * gamma * lii;
+}
+
+__global__ void k_poisson_weights(int64_t count, const int64_t *dd, const int64_t *ii,
+                                  int prec, int64_t D, int64_t M, const double *lam,
+                                  const int32_t *lo, const int32_t *hi, const int64_t *aoff,
+                                  const double *anc, const float *anc_f, const double *rinv,
+                                  const float *rinv_f, double *out)
+{
+    const int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (k >= count) return;
+    const int64_t d = dd[k], i = ii[k];
+    if (d < 0 || d >= D || i < 0 || i >= M) { out[k] = 0.0; return; }
+    out[k] = prec == TOMO_PREC_FP64
+                 ? weight_from_anchor_d(d, i, lam, lo, hi, aoff, anc, rinv)
+                 : double(weight_from_anchor_f(d, i, lam, lo, hi, aoff, anc_f, rinv_f));
+}
+
+static inline unsigned blocks_for(int64_t n, int t) { return unsigned((n + t - 1) / t); }
+
+cudaError_t launch_plan_tables(Plan &p)
+{
+    cudaError_t e;
+    int64_t *cnt = nullptr;
+    void *tmp = nullptr;
+    size_t tmp_bytes = 0;
+    if ((e = cudaMalloc(&cnt, sizeof(int64_t) * (p.D + 1))) != cudaSuccess) return e;
+    k_bands<<<blocks_for(p.D, 256), 256, 0, p.stream>>>(p.D, p.M, p.band_k, p.lam, p.lo, p.hi, cnt);
+    count_launch();
+    cudaMemsetAsync(cnt + p.D, 0, sizeof(int64_t), p.stream);
+    cub::DeviceScan::ExclusiveSum(nullptr, tmp_bytes, cnt, p.aoff, p.D + 1, p.stream);
+    if ((e = cudaMalloc(&tmp, tmp_bytes)) != cudaSuccess) { cudaFree(cnt); return e; }
+    cub::DeviceScan::ExclusiveSum(tmp, tmp_bytes, cnt, p.aoff, p.D + 1, p.stream);
+    count_launch();
+    int64_t total = 0;
+    cudaMemcpyAsync(&total, p.aoff + p.D, sizeof(int64_t), cudaMemcpyDeviceToHost, p.stream);
+    e = cudaStreamSynchronize(p.stream);
+    cudaFree(tmp);
+    cudaFree(cnt);
+    if (e != cudaSuccess) return e;
+    p.n_anchor = total;
+    const int64_t na = total > 0 ? total : 1;
+    if ((e = cudaMalloc(&p.anchor, sizeof(double) * na)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&p.anchor_f, sizeof(float) * na)) != cudaSuccess) return e;
+    k_anchors<<<blocks_for(p.D, 128), 128, 0, p.stream>>>(p.D, p.lam, p.lo, p.hi, p.aoff,
+                                                          p.anchor, p.anchor_f);
+    count_launch();
+    const int64_t nr = p.M + RUN + 1;
+    k_ratio_inv<<<blocks_for(nr, 256), 256, 0, p.stream>>>(nr, p.ratio_inv, p.ratio_inv_f);
+    count_launch();
+    k_fwd_tiles<<<blocks_for(p.fwd_tiles, 128), 128, 0, p.stream>>>(p.D, p.fwd_tiles, p.lo,
+                                                                    p.hi, p.fwd_klo, p.fwd_khi);
+    count_launch();
+    k_adj_tiles<<<blocks_for(p.adj_tiles, 128), 128, 0, p.stream>>>(p.D, p.M, p.adj_tiles, p.lo,
+                                                                    p.hi, p.adj_dlo, p.adj_dhi);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hess_diag(Plan &p)
+{
+    k_hess_diag<<<blocks_for(p.M, 128), 128, 0, p.stream>>>(
+        p.M, p.gamma, p.lam, p.lo, p.hi, p.aoff, p.anchor, p.ratio_inv, p.adj_dlo, p.adj_dhi, p.h);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_poisson_weights(Plan &p, const int64_t *d, const int64_t *i, int64_t count,
+                                   double *out)
+{
+    if (count <= 0) return cudaSuccess;
+    k_poisson_weights<<<blocks_for(count, 128), 128, 0, p.stream>>>(
+        count, d, i, p.precision, p.D, p.M, p.lam, p.lo, p.hi, p.aoff, p.anchor, p.anchor_f,
+        p.ratio_inv, p.ratio_inv_f, out);
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace tomo

@@ -1,0 +1,128 @@
+// tomo_internal.cuh -- internal declarations shared by the CUDA translation
+// units of libtomo (plan kernels, band contractions, row kernels, host API).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/tomo.h"
+
+namespace tomo {
+
+// ---------------------------------------------------------------------------
+// Geometry of the band contraction tiles.
+//   Forward  O = F X : CTA tile of FWD_BD probes x BN columns, K steps of BK
+//                      photon numbers inside the tile's union band.
+//   Adjoint  Z = F^T Y : CTA tile of ADJ_BI photon numbers x BN columns,
+//                      steps of ADJ_BKD probes inside the tile's probe range.
+// Poisson weights are generated in runs of RUN consecutive photon numbers
+// from an anchor stored every RUN photon numbers (see plan.cu).
+// ---------------------------------------------------------------------------
+constexpr int RUN = 8;
+constexpr int FWD_BD = 64;
+constexpr int FWD_BK = 32;
+constexpr int ADJ_BI = 64;
+constexpr int ADJ_BKD = 32;
+constexpr int GEMM_THREADS = 256;
+constexpr int ROW_WARPS = 8;              // warps per CTA in row kernels
+constexpr int MAX_N = 1024;               // outcomes supported by row kernels
+constexpr int RED_SLOTS = 4;              // partial-sum slots per reduction
+
+// Device-resident scalars of the solver.  Written by the last CTA of the
+// kernel that produces them (no host round trip between kernels).
+struct DevScalars {
+    // CG
+    double rz, rr, pq, alpha, beta, bn, tol;
+    int32_t cg_active, cg_iters, max_cg, pad0;
+    // Newton iteration set-up
+    double kkt2, w2, eps, gdir;
+    int32_t use_grad_dir, pad1;
+    // line search
+    double alpha_ls, gts, reg, dres, f_trial;
+    int32_t neg, accept, ls_go, pad2;
+    // objective pieces
+    double res2, regval, nonfinite;
+    // counters for the last-block reductions (one per concurrent site)
+    unsigned int ticket[4];
+};
+
+struct Plan {
+    int64_t M, N, D;
+    double gamma, band_k;
+    int precision;
+    cudaStream_t stream;
+    bool own_stream;
+    int device;
+    int num_sms;
+
+    // problem tables (device)
+    double *lam;       // D
+    int32_t *lo, *hi;  // D, inclusive band; empty band: lo = M, hi = M - 1
+    int64_t *aoff;     // D + 1 offsets into the anchor table
+    double *anchor;    // F_{d, a0_d + RUN j}, a0_d = lo_d rounded down to RUN
+    float *anchor_f;   // same, rounded to float
+    double *ratio_inv; // M + 1: 1/(i) for i >= 1 (ratio_inv[0] unused)
+    float *ratio_inv_f;
+    int32_t *fwd_klo, *fwd_khi;  // per forward tile (probes)
+    int32_t *adj_dlo, *adj_dhi;  // per adjoint tile (photon numbers)
+    double *h;         // M: Hessian diagonal
+    int64_t n_anchor;
+    int fwd_tiles, adj_tiles;
+
+    // workspaces (device), M x N unless noted
+    double *Th, *trial, *s, *G, *g, *x, *r, *z, *p, *u, *q, *dir;
+    double *R, *Rt, *O;      // D x N
+    double *Pbuf;            // D x N staging of a host P
+    double *Xbuf;            // M x N staging of host Theta / grad
+    uint8_t *freem, *var;    // M x N masks
+    int32_t *mrow;           // M
+    double *partials;        // RED_SLOTS x max_partials
+    int64_t max_partials;
+    DevScalars *sc;          // device scalars
+    DevScalars *sc_host;     // pinned mirror
+    double *scratch_host;    // pinned host scratch (small)
+    int64_t *idx_buf;        // scratch for tomo_poisson_weights
+    double *val_buf;
+    int64_t idx_cap;
+};
+
+// ------------------------------- launchers ---------------------------------
+// plan.cu
+cudaError_t launch_plan_tables(Plan &p);
+cudaError_t launch_hess_diag(Plan &p);
+cudaError_t launch_poisson_weights(Plan &p, const int64_t *d, const int64_t *i,
+                                   int64_t count, double *out);
+
+// band_gemm.cu
+enum FwdMode { FWD_STORE = 0, FWD_RESID = 1, FWD_DELTA = 2 };
+enum AdjMode { ADJ_STORE = 0, ADJ_GRAD = 1, ADJ_HESS = 2 };
+// O = F X (mode STORE); R = F X - P with sum R^2 (RESID); Rt = R + F X with
+// sum (2 R . FX + FX^2) (DELTA).  `prec` selects double or float arithmetic.
+cudaError_t launch_forward(Plan &p, int prec, FwdMode mode, const double *X, double *out,
+                           const double *P_or_R, bool gated);
+cudaError_t launch_forward_gated_ls(Plan &p, int prec, FwdMode mode, const double *X, double *out,
+                                   const double *P_or_R);
+// Z = F^T Y (STORE); G = 2 F^T Y + 2 gamma L Xreg (GRAD / HESS: same formula,
+// HESS is gated by the CG-active flag).
+cudaError_t launch_adjoint(Plan &p, int prec, AdjMode mode, const double *Y, double *out,
+                           const double *Xreg, bool gated);
+
+// rowops.cu
+cudaError_t launch_fill(Plan &p, double *x, double v, int64_t n);
+cudaError_t launch_regulariser(Plan &p, const double *X);   // -> sc->regval
+cudaError_t launch_project_rows(Plan &p, const double *X, double *Y);
+cudaError_t launch_kkt(Plan &p, const double *Th, const double *G);  // -> sc->kkt2
+cudaError_t launch_setup1(Plan &p, int stage, double eps_bar);  // kkt2, w2, eps, g, var, mrow
+cudaError_t launch_setup2(Plan &p, int stage, int max_cg);      // I mask, CG start
+cudaError_t launch_cg_restrict(Plan &p, int stage);
+cudaError_t launch_cg_update_xr(Plan &p, int stage);
+cudaError_t launch_cg_update_p(Plan &p, int stage);
+cudaError_t launch_direction(Plan &p, int stage);
+cudaError_t launch_trial(Plan &p, int stage, double alpha, bool delta_mode);
+cudaError_t launch_set_grad_dir(Plan &p);
+cudaError_t launch_nonfinite_check(Plan &p, const double *x, int64_t n, int slot);
+
+// kernel launch accounting (all threads)
+void count_launch(int n = 1);
+
+}  // namespace tomo

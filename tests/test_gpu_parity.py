@@ -1,0 +1,325 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle,
+element by element on the same seeded inputs: every step of the hot path on
+sizes spanning several tiles with ragged tails, the full solver, the full-size
+configurations on sampled outputs, edge cases and error paths."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+# FP64 products: both sides sum the same terms in double (different order and
+# a different but 1e-15-accurate evaluation of the Poisson weights).
+TOL64 = 1e-12
+# FP32 products: weights carry <= 8 float roundings (anchor + ratio
+# recurrence, ~5e-7 relative) and sums of up to ~3000 terms accumulate in
+# float (<= ~3000 * 6e-8 worst case, ~1e-6 typical).
+TOL32 = 2e-5
+
+
+@pytest.fixture(scope="module")
+def tomo():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2404_02844_gb300 as t
+    from paper_2404_02844_gb300 import build
+    build.build()
+    t.lib()
+    return t
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def ragged_case(M=300, N=37, D=333, X=250.0, band_k=10.0, gamma=1e-2, seed=5):
+    lam = workloads.probe_intensities(D, X)
+    rng = np.random.default_rng(seed)
+    return lam, rng, dict(M=M, N=N, band_k=band_k, gamma=gamma)
+
+
+CASES = {
+    "ragged": dict(M=300, N=37, D=333, X=250.0, band_k=10.0, gamma=1e-2),
+    "dense_small": dict(M=64, N=9, D=100, X=30.0, band_k=0.0, gamma=1e-3),
+    "wide_N": dict(M=200, N=129, D=150, X=150.0, band_k=10.0, gamma=0.0),
+    "narrow_band": dict(M=513, N=8, D=700, X=480.0, band_k=3.0, gamma=0.3),
+    "beyond_cutoff": dict(M=100, N=5, D=90, X=200.0, band_k=10.0, gamma=1e-2),
+}
+
+
+def make(case, seed=1):
+    c = CASES[case]
+    lam = workloads.probe_intensities(c["D"], c["X"])
+    return lam, np.random.default_rng(seed), c
+
+
+def abs_scale_F(pr, X):
+    return pr.apply_F(np.abs(X))
+
+
+def abs_scale_Ft(pr, Y):
+    return pr.apply_Ft(np.abs(Y))
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_bands_bit_exact(tomo, case):
+    lam, rng, c = make(case)
+    pr = oracle.Problem(c["M"], c["N"], lam, c["band_k"], c["gamma"])
+    with tomo.Plan(c["M"], c["N"], lam, c["band_k"], c["gamma"]) as pl:
+        lo, hi = pl.bands()
+    lo_o, hi_o = pr.bands()
+    np.testing.assert_array_equal(lo, lo_o)
+    np.testing.assert_array_equal(hi, hi_o)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-13), ("fp32", 1e-6)])
+def test_poisson_weights(tomo, prec, tol):
+    lam, rng, c = make("ragged")
+    with tomo.Plan(c["M"], c["N"], lam, c["band_k"], c["gamma"], precision=prec) as pl:
+        lo, hi = pl.bands()
+        d = rng.integers(0, len(lam), 4000)
+        i = np.clip(lo[d] + rng.integers(-3, 400, 4000), 0, c["M"] - 1)
+        got = pl.poisson_weights(d, i)
+    ref = np.array([oracle.poisson(ii, lam[dd]) if lo[dd] <= ii <= hi[dd] else 0.0
+                    for dd, ii in zip(d, i)])
+    assert np.all((ref == 0) == (got == 0))
+    nz = ref > 1e-300
+    rel = np.abs(got[nz] - ref[nz]) / ref[nz]
+    # in float, weights below ~1e-38 lose relative accuracy (subnormal range)
+    if prec == "fp32":
+        rel = rel[ref[nz] > 1e-30]
+    assert rel.max() <= tol, rel.max()
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_apply_F_Ft_hvp(tomo, case, prec):
+    lam, rng, c = make(case)
+    M, N, D = c["M"], c["N"], len(lam)
+    tol = TOL64 if prec == "fp64" else TOL32
+    pr = oracle.Problem(M, N, lam, c["band_k"], c["gamma"])
+    X = rng.standard_normal((M, N))
+    Y = rng.standard_normal((D, N))
+    with tomo.Plan(M, N, lam, c["band_k"], c["gamma"], precision=prec) as pl:
+        O = host(pl.apply_F(dev(X)))
+        Z = host(pl.apply_Ft(dev(Y)))
+        HV = host(pl.hvp(dev(X)))
+    O_ref = pr.apply_F(X)
+    Z_ref = pr.apply_Ft(Y)
+    assert np.all(np.abs(O - O_ref) <= tol * abs_scale_F(pr, X) + 1e-300)
+    assert np.all(np.abs(Z - Z_ref) <= tol * abs_scale_Ft(pr, Y) + 1e-300)
+    HV_ref = pr.hvp(X)
+    scale = 2 * pr.apply_Ft(pr.apply_F(np.abs(X))) + 8 * c["gamma"] * np.abs(X).max()
+    assert np.all(np.abs(HV - HV_ref) <= tol * scale + 1e-300)
+
+
+def test_hess_diag(tomo):
+    for case in CASES:
+        lam, rng, c = make(case)
+        pr = oracle.Problem(c["M"], c["N"], lam, c["band_k"], c["gamma"])
+        with tomo.Plan(c["M"], c["N"], lam, c["band_k"], c["gamma"]) as pl:
+            h = pl.hess_diag()
+        np.testing.assert_allclose(h, pr.hess_diag(), rtol=1e-13, atol=0)
+
+
+@pytest.mark.parametrize("N", [2, 3, 9, 32, 33, 100, 128, 257, 1024])
+def test_project_simplex(tomo, N):
+    rng = np.random.default_rng(N)
+    M = 301
+    X = rng.standard_normal((M, N)) * rng.choice([0.01, 1.0, 30.0], (M, 1))
+    X[0] = 1.0 / N                    # already on the simplex
+    X[1] = 5.0                        # all equal
+    X[2] = 0.0
+    X[2, N // 2] = 10.0               # one dominant entry
+    with tomo.Plan(M, N, np.zeros(1), 10.0, 0.0) as pl:
+        Y = host(pl.project_simplex(dev(X)))
+    Y_ref = np.stack([oracle.project_simplex(x) for x in X])
+    np.testing.assert_allclose(Y, Y_ref, rtol=0, atol=1e-14 * max(1.0, np.abs(X).max()))
+    assert Y.min() >= 0.0
+    np.testing.assert_allclose(Y.sum(1), 1.0, atol=1e-13 * N)
+
+
+def test_objective_gradient_kkt(tomo):
+    w = workloads.small_case(M=200, bins=15, D=260, X=180.0, gamma=5e-3, seed=11)
+    pr = oracle.Problem.from_workload(w)
+    rng = np.random.default_rng(3)
+    Th = workloads.random_feasible_theta(w.M, w.N, rng)
+    f_ref, G_ref = pr.gradient(w.P, Th)
+    for prec, tol in (("fp64", 1e-12), ("fp32", 2e-5)):
+        with tomo.Plan.from_workload(w, precision=prec) as pl:
+            # device buffers
+            f, G = pl.objective(dev(w.P), dev(Th), want_grad=True)
+            assert f == pytest.approx(f_ref, rel=1e-12)   # objective is always double
+            G = host(G)
+            scale = 2 * pr.apply_Ft(np.abs(pr.residual(w.P, Th))) + 8 * w.gamma
+            assert np.all(np.abs(G - G_ref) <= tol * scale)
+            # host buffers give the same
+            f2, G2 = pl.objective(w.P, Th, want_grad=True)
+            assert f2 == f
+            np.testing.assert_array_equal(G2, G)
+            k = pl.kkt(dev(Th), dev(G_ref))
+            assert k == pytest.approx(pr.kkt(Th, G_ref), rel=1e-12)
+
+
+def load_gold(name):
+    with open(os.path.join(GOLD, f"fstar_{name}.json")) as fh:
+        return json.load(fh)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_fit_c1_matches_certified_optimum(tomo, prec):
+    w = workloads.config_c1()
+    gold = load_gold("c1")
+    with tomo.Plan.from_workload(w, precision=prec) as pl:
+        Th, rep = pl.fit(dev(w.P), eps_kkt=1e-12)
+    Th = host(Th)
+    pr = oracle.Problem.from_workload(w)
+    f = pr.objective(w.P, Th)
+    gap = (f - gold["f_star"]) / gold["f_star"]
+    assert gap <= 1e-8, (gap, rep)
+    assert rep["f"] == pytest.approx(f, rel=1e-12)
+    assert np.abs(Th.sum(1) - 1).max() <= 1e-13 * w.N
+    assert Th.min() >= 0.0
+    rows = gold["sample_rows"]
+    np.testing.assert_allclose(Th[rows], np.array(gold["theta_rows"]), atol=gold["theta_tol"])
+
+
+def test_fit_fp64_follows_oracle_iterates(tomo):
+    """The plain FP64 path makes the oracle's decisions: after k Newton
+    iterations both hold the same iterate (up to rounding)."""
+    w = workloads.small_case(M=120, bins=9, D=150, X=100.0, gamma=1e-2, seed=21)
+    pr = oracle.Problem.from_workload(w)
+    with tomo.Plan.from_workload(w, precision="fp64") as pl:
+        for k in (1, 2, 3, 6):
+            Th_o, rep_o, _ = pr.fit(w.P, max_newton=k, eps_kkt=0.0)
+            Th_g, rep_g = pl.fit(dev(w.P), max_newton=k, eps_kkt=0.0)
+            Th_g = host(Th_g)
+            assert (rep_g["iters_s1"], rep_g["iters_s2"]) == (rep_o["iters_s1"], rep_o["iters_s2"])
+            assert rep_g["f"] == pytest.approx(rep_o["f"], rel=1e-9)
+            np.testing.assert_allclose(Th_g, Th_o, atol=1e-8)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_fit_small_cases_reach_oracle_optimum(tomo, prec):
+    for seed, kw in ((31, dict(M=96, bins=11, D=128, X=80.0, gamma=1e-3)),
+                     (32, dict(M=77, bins=4, D=61, X=60.0, gamma=0.0, band_k=0.0)),
+                     (33, dict(M=150, bins=20, D=200, X=140.0, gamma=1e-1, p_dark=1e-3))):
+        w = workloads.small_case(seed=seed, **kw)
+        pr = oracle.Problem.from_workload(w)
+        _, rep_o, _ = pr.fit(w.P, eps_kkt=1e-12, max_newton=3000)
+        with tomo.Plan.from_workload(w, precision=prec) as pl:
+            Th, rep = pl.fit(dev(w.P), eps_kkt=1e-12, max_newton=3000)
+        f = pr.objective(w.P, host(Th))
+        assert (f - rep_o["f"]) / rep_o["f"] <= 1e-8, (seed, f, rep_o["f"], rep)
+
+
+def test_fit_host_buffers_and_warm_start(tomo):
+    w = workloads.config_c1()
+    with tomo.Plan.from_workload(w) as pl:
+        Th, rep = pl.fit(w.P, eps_kkt=1e-12)            # numpy in, numpy out
+        assert isinstance(Th, np.ndarray)
+        Th2, rep2 = pl.fit(w.P, Theta=Th.copy(), eps_kkt=1e-12)   # warm start at the optimum
+        assert rep2["iters_s1"] + rep2["iters_s2"] <= 3
+        assert rep2["f"] <= rep["f"] * (1 + 1e-12)
+        # stage 2 only (Algorithm 1) from the uniform start converges too
+        Th3, rep3 = pl.fit(dev(w.P), start_stage=2, eps_kkt=1e-11, max_newton=3000)
+        assert rep3["iters_s1"] == 0
+        assert (rep3["f"] - rep["f"]) / rep["f"] <= 1e-8
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_fit_c2_full_size(tomo, prec):
+    path = os.path.join(GOLD, "fstar_c2.json")
+    if not os.path.exists(path):
+        pytest.skip("certified c2 optimum not generated")
+    gold = load_gold("c2")
+    w = workloads.config_c2()
+    with tomo.Plan.from_workload(w, precision=prec) as pl:
+        P = dev(w.P)
+        Th, rep = pl.fit(P, f_target=gold["f_star"] * (1 + 0.5e-8))
+        f = pl.objective(P, Th)
+    assert rep["stop_name"] in ("f_target", "kkt"), rep
+    gap = (f - gold["f_star"]) / gold["f_star"]
+    assert gap <= 1e-8, (gap, rep)
+    Th = host(Th)
+    assert np.abs(Th.sum(1) - 1).max() <= 1e-13 * w.N
+    assert Th.min() >= 0.0
+
+
+def test_c3_scale_products_on_sampled_rows(tomo):
+    """Full c3 size (M = D = 1e6, N = 100, band +-10 sqrt(lambda)): products
+    through the C ABI, checked on sampled output rows computed one by one
+    by the oracle."""
+    M, N, D = 1_000_000, 100, 1_000_000
+    lam = workloads.probe_intensities(D, 9e5)
+    rng = np.random.default_rng(7)
+    X = rng.random((M, N))
+    X /= X.sum(1, keepdims=True)
+    pr = oracle.Problem(M, N, lam, 10.0, 0.0, store_F=False)
+    rows_d = np.unique(np.concatenate([[0, 1, D // 3, D - 1], rng.integers(0, D, 12)]))
+    rows_i = np.unique(np.concatenate([[0, 5000, M // 2, M - 1], rng.integers(0, M, 12)]))
+    Xd = dev(X)
+    for prec, tol in (("fp32", TOL32), ("fp64", TOL64)):
+        with tomo.Plan(M, N, lam, 10.0, 0.0, precision=prec) as pl:
+            O = pl.apply_F(Xd)
+            O_rows = host(O[torch.from_numpy(rows_d).cuda()])
+            Z = pl.apply_Ft(O)
+            Z_rows = host(Z[torch.from_numpy(rows_i).cuda()])
+            Oh = host(O) if prec == "fp32" else None
+            del O, Z
+        ref = pr.apply_F_rows(X, rows_d)
+        scale = pr.apply_F_rows(np.abs(X), rows_d)
+        assert np.all(np.abs(O_rows - ref) <= tol * scale + 1e-300), prec
+        if Oh is not None:
+            refz = pr.apply_Ft_rows(Oh, rows_i)
+            scalez = pr.apply_Ft_rows(np.abs(Oh), rows_i)
+            assert np.all(np.abs(Z_rows - refz) <= tol * scalez + 1e-300)
+        del Xd
+        Xd = dev(X)
+
+
+def test_degenerate_problems(tomo):
+    # one photon number: Theta is any simplex row; f is minimised there
+    lam = np.array([0.0, 0.5, 1.0])
+    P = np.array([[0.6, 0.4], [0.5, 0.5], [0.2, 0.8]])
+    pr = oracle.Problem(1, 2, lam, 10.0, 0.0)
+    Th_o, rep_o, _ = pr.fit(P, eps_kkt=1e-14)
+    with tomo.Plan(1, 2, lam, 10.0, 0.0) as pl:
+        Th, rep = pl.fit(P, eps_kkt=1e-14)
+    np.testing.assert_allclose(Th, Th_o, atol=1e-10)
+    # a single probe, vacuum only (lambda = 0): F = e_0
+    with tomo.Plan(5, 3, np.zeros(1), 10.0, 0.1) as pl:
+        Th, rep = pl.fit(np.array([[0.2, 0.3, 0.5]]), eps_kkt=1e-13)
+        assert np.abs(Th.sum(1) - 1).max() < 1e-14
+
+
+def test_error_paths(tomo):
+    w = workloads.config_c1()
+    P = w.P.copy()
+    P[3, 2] = np.nan
+    with tomo.Plan.from_workload(w) as pl:
+        with pytest.raises(tomo.TomoError) as e:
+            pl.fit(dev(P))
+        assert e.value.status == 6
+        with pytest.raises(tomo.TomoError) as e:
+            pl.fit(dev(w.P), beta=1.5)
+        assert e.value.status == 1
+        # the plan is still usable after the errors
+        Th, rep = pl.fit(dev(w.P), eps_kkt=1e-10)
+        assert rep["status"] == "TOMO_OK"
+    with pytest.raises(tomo.TomoError) as e:
+        tomo.Plan(10, 3, np.array([3.0, 1.0]), 10.0, 0.0)
+    assert e.value.status == 1
