@@ -88,6 +88,8 @@ def lib():
         L.orc_project_simplex_sort.argtypes = [c_ptr, c_i64, c_ptr]
         L.orc_project_simplex_condat.argtypes = [c_ptr, c_i64, c_ptr]
         L.orc_project_rows.argtypes = [c_ptr, c_ptr, c_ptr]
+        L.orc_fw_gap.restype = c_dbl
+        L.orc_fw_gap.argtypes = [c_ptr, c_ptr, c_ptr]
         L.orc_kkt.restype = c_dbl
         L.orc_kkt.argtypes = [c_ptr, c_ptr, c_ptr]
         L.orc_default_opts.argtypes = [ctypes.POINTER(_Opts)]
@@ -230,6 +232,10 @@ class Problem:
 
     def kkt(self, Theta, G) -> float:
         return lib().orc_kkt(self._h, _p(_f64(Theta)), _p(_f64(G)))
+
+    def fw_gap(self, Theta, G) -> float:
+        """Upper bound of f(Theta) - f* for a feasible Theta (convexity)."""
+        return lib().orc_fw_gap(self._h, _p(_f64(Theta)), _p(_f64(G)))
 
     # --- solver --------------------------------------------------------
     @staticmethod

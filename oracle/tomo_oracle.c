@@ -445,6 +445,28 @@ ORC_API double orc_kkt(const orc_problem *p, const double *Th, const double *G)
     return sqrt(s / ((double)N * (double)M));
 }
 
+/* Frank-Wolfe duality gap of a feasible Theta: f is convex on the product of
+ * row simplices, so for every feasible Theta', f(Theta') >= f(Theta) +
+ * <G, Theta' - Theta>, whose minimum over the simplices puts each row's mass
+ * on its smallest gradient entry.  Hence
+ *     f(Theta) - f* <= sum_i ( <G_i, Theta_i> - min_n G_{i,n} ),
+ * a certificate of the optimum that needs no knowledge of f*. */
+ORC_API double orc_fw_gap(const orc_problem *p, const double *Th, const double *G)
+{
+    const int64_t M = p->M, N = p->N;
+    double s = 0.0;
+#pragma omp parallel for reduction(+ : s)
+    for (int64_t i = 0; i < M; ++i) {
+        double mn = G[i * N], dot = 0.0;
+        for (int64_t n = 0; n < N; ++n) {
+            if (G[i * N + n] < mn) mn = G[i * N + n];
+            dot += G[i * N + n] * Th[i * N + n];
+        }
+        s += dot - mn;
+    }
+    return s;
+}
+
 /* ---------------------------------------------------------------------- */
 /* Two-stage two-metric projected truncated Newton (Algorithms 1, 2, 3)    */
 /* ---------------------------------------------------------------------- */

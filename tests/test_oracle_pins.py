@@ -298,6 +298,28 @@ def brute_force_qp(F, P, gamma):
     return best
 
 
+def test_fw_gap_bounds_the_objective_gap():
+    """Convexity: f(Theta) - f* <= FW gap for every feasible Theta, and the
+    gap vanishes at the brute-force optimum."""
+    rng = np.random.default_rng(8)
+    M, N, D = 4, 3, 9
+    lam = np.sort(rng.uniform(0.0, 6.0, D))
+    P = rng.dirichlet(np.ones(N), D)
+    pr = oracle.Problem(M, N, lam, 0.0, 0.05)
+    T_ref = brute_force_qp(dense_F(M, lam, 0.0), P, 0.05)
+    f_star = pr.objective(P, T_ref)
+    _, G = pr.gradient(P, T_ref)
+    assert pr.fw_gap(T_ref, G) <= 1e-10
+    for _ in range(50):
+        Th = workloads.random_feasible_theta(M, N, rng)
+        f, G = pr.gradient(P, Th)
+        gap = pr.fw_gap(Th, G)
+        assert f - f_star <= gap * (1 + 1e-12) + 1e-15
+        # definition on a hand case: one row, G = (1, 3), Theta = (0.5, 0.5): 2 - 1 = 1
+    h = oracle.Problem(1, 2, np.array([1.0]), 0.0, 0.0)
+    assert h.fw_gap(np.array([[0.5, 0.5]]), np.array([[1.0, 3.0]])) == 1.0
+
+
 @pytest.mark.parametrize("seed", [1, 2, 3])
 def test_fit_matches_brute_force_qp(seed):
     rng = np.random.default_rng(seed)
