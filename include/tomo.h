@@ -44,7 +44,7 @@ typedef enum {
     TOMO_ENOMEM = 2,     /* device or host allocation failed */
     TOMO_ECUDA = 3,      /* a CUDA runtime call failed */
     TOMO_ENOTCONV = 4,   /* iteration cap reached before the stopping rule */
-    TOMO_ETIMEOUT = 5,   /* reserved: a bounded device wait gave up */
+    TOMO_ETIMEOUT = 5,   /* a bounded device wait (tensor-core pipeline) gave up */
     TOMO_ENONFINITE = 6  /* P or Theta holds NaN/Inf, or the objective became non-finite */
 } tomo_status;
 
@@ -57,7 +57,17 @@ typedef enum {
  *         R <- R + F s for each accepted step s; line searches use the exact
  *         quadratic expansion f(Theta + s) - f(Theta) = 2<R, F s> + ||F s||^2
  *         + g(Theta + s) - g(Theta) reduced in double. */
-typedef enum { TOMO_PREC_FP64 = 0, TOMO_PREC_FP32 = 1 } tomo_precision;
+/*   MIXED: as FP32 for the CG Hessian products and the line-search products,
+ *         but the gradient F^T R is contracted in double.
+ *   TC:   as MIXED, but the CG Hessian products run on the tensor cores
+ *         (tcgen05.mma, bf16 operands split into hi + lo parts, three products
+ *         per slice, f32 accumulation in tensor memory: ~16 significant bits). */
+typedef enum {
+    TOMO_PREC_FP64 = 0,
+    TOMO_PREC_FP32 = 1,
+    TOMO_PREC_MIXED = 2,
+    TOMO_PREC_TC = 3
+} tomo_precision;
 
 typedef struct tomo_plan_s *tomo_plan_t;
 
@@ -162,13 +172,15 @@ tomo_status tomo_fit(tomo_plan_t plan, const double *P, double *Theta,
  * same kernels. */
 
 /* O = F X (Table ops, the F Pi product of the objective): X M x N -> O D x N,
- * computed in the plan's precision, stored in double. */
+ * computed in the precision of the plan's Hessian products (double for FP64
+ * plans, float otherwise), stored in double. */
 tomo_status tomo_apply_F(tomo_plan_t plan, const double *X, double *O);
 
 /* Z = F^T Y: Y D x N -> Z M x N, plan precision, stored in double. */
 tomo_status tomo_apply_Ft(tomo_plan_t plan, const double *Y, double *Z);
 
-/* Hessian product (Table ops): HV = 2 F^T F V + 2 gamma L V, M x N. */
+/* Hessian product (Table ops): HV = 2 F^T F V + 2 gamma L V, M x N, in the
+ * arithmetic of the plan's CG products (tensor cores for TC plans). */
 tomo_status tomo_hvp(tomo_plan_t plan, const double *V, double *HV);
 
 /* Hessian diagonal h_i = 2 sum_d F_{d,i}^2 + 2 gamma L_ii (Table ops), M

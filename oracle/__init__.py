@@ -38,7 +38,7 @@ def build(force: bool = False) -> str:
     # -ffp-contract=off: products and sums are rounded as written (no fused
     # multiply-add), so integer decisions such as the band bounds are those of
     # the plain IEEE evaluation on every host architecture
-    cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11", "-ffp-contract=off",
+    cmd = ["gcc", "-O3", "-fopenmp", "-fPIC", "-shared", "-std=c11", "-ffp-contract=off",
            "-o", tmp, _SRC, "-lm"]
     subprocess.check_call(cmd)
     os.replace(tmp, _LIB)

@@ -168,11 +168,11 @@ ORC_API void orc_apply_F(const orc_problem *p, const double *X, double *O)
     const int64_t N = p->N;
 #pragma omp parallel for schedule(dynamic, 8)
     for (int64_t d = 0; d < p->D; ++d) {
-        double *o = O + d * N;
+        double *restrict o = O + d * N;
         for (int64_t n = 0; n < N; ++n) o[n] = 0.0;
         for (int64_t i = p->lo[d]; i <= p->hi[d]; ++i) {
-            double f = Fval(p, d, i);
-            const double *x = X + i * N;
+            const double f = Fval(p, d, i);
+            const double *restrict x = X + i * N;
             for (int64_t n = 0; n < N; ++n) o[n] += f * x[n];
         }
     }
@@ -221,12 +221,12 @@ ORC_API void orc_apply_Ft(const orc_problem *p, const double *Y, double *Z)
     const int64_t N = p->N;
 #pragma omp parallel for schedule(dynamic, 8)
     for (int64_t i = 0; i < p->M; ++i) {
-        double *z = Z + i * N;
+        double *restrict z = Z + i * N;
         for (int64_t n = 0; n < N; ++n) z[n] = 0.0;
         for (int64_t d = p->dlo[i]; d <= p->dhi[i]; ++d) {
             if (i < p->lo[d] || i > p->hi[d]) continue;
-            double f = Fval(p, d, i);
-            const double *y = Y + d * N;
+            const double f = Fval(p, d, i);
+            const double *restrict y = Y + d * N;
             for (int64_t n = 0; n < N; ++n) z[n] += f * y[n];
         }
     }

@@ -26,6 +26,8 @@ __all__ = ["Plan", "TomoError", "lib", "tomo_plan", "tomo_plan_destroy", "tomo_o
 
 PREC_FP64 = 0
 PREC_FP32 = 1
+PREC_MIXED = 2
+PREC_TC = 3
 STATUS = {0: "TOMO_OK", 1: "TOMO_EINVAL", 2: "TOMO_ENOMEM", 3: "TOMO_ECUDA",
           4: "TOMO_ENOTCONV", 5: "TOMO_ETIMEOUT", 6: "TOMO_ENONFINITE"}
 STOP = {0: "kkt", 1: "f_target", 2: "iteration_cap", 3: "stagnated"}
@@ -214,7 +216,7 @@ class Plan:
         lam = np.ascontiguousarray(lam, dtype=np.float64)
         self.M, self.N, self.D = int(M), int(N), int(lam.shape[0])
         self.band_k, self.gamma = float(band_k), float(gamma)
-        self.precision = {"fp64": PREC_FP64, "fp32": PREC_FP32}[precision] \
+        self.precision = {"fp64": PREC_FP64, "fp32": PREC_FP32, "mixed": PREC_MIXED, "tc": PREC_TC}[precision] \
             if isinstance(precision, str) else int(precision)
         if stream is None:
             try:

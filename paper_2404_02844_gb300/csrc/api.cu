@@ -5,6 +5,7 @@
 // band_gemm.cu / rowops.cu and only scalar decisions on the host.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cstdarg>
 #include <chrono>
@@ -14,6 +15,7 @@
 #include <new>
 #include <string>
 #include <utility>
+#include <vector>
 
 #include "tomo_internal.cuh"
 
@@ -72,11 +74,22 @@ static void free_plan(Plan *p)
 {
     if (!p) return;
     void *dev[] = {p->lam, p->lo, p->hi, p->aoff, p->anchor, p->anchor_f, p->ratio_inv,
-                   p->ratio_inv_f, p->fwd_klo, p->fwd_khi, p->adj_dlo, p->adj_dhi, p->h,
+                   p->ratio_inv_f2, p->lam_f2, p->fwd_klo, p->fwd_khi, p->adj_dlo, p->adj_dhi, p->h,
                    p->Th, p->trial, p->s, p->G, p->g, p->x, p->r, p->z, p->p, p->u, p->q,
                    p->dir, p->R, p->Rt, p->O, p->Pbuf, p->Xbuf, p->freem, p->var, p->mrow,
                    p->partials, p->sc, p->idx_buf, p->val_buf};
     for (void *d : dev)
+        if (d) cudaFree(d);
+    auto free_sched = [](Schedule &s) {
+        void *sd[] = {s.units, s.tile_first, s.tile_nsplit, s.counters, s.part};
+        for (void *d : sd)
+            if (d) cudaFree(d);
+    };
+    for (auto &row : p->sched)
+        for (Schedule &s : row) free_sched(s);
+    for (Schedule &s : p->sched_tc) free_sched(s);
+    void *mir[] = {p->ut_hi, p->ut_lo, p->ot_hi, p->ot_lo};
+    for (void *d : mir)
         if (d) cudaFree(d);
     if (p->sc_host) cudaFreeHost(p->sc_host);
     if (p->scratch_host) cudaFreeHost(p->scratch_host);
@@ -114,6 +127,124 @@ static tomo_status check_finite(Plan &p, const double *x, int64_t n, const char 
     if (p.sc_host->nonfinite > 0.0)
         return fail(TOMO_ENONFINITE, "%s holds %.0f non-finite values", what, p.sc_host->nonfinite);
     return TOMO_OK;
+}
+
+// Work-unit schedules of the band contractions (split-K): the reduction
+// range of every tile (union band of a probe tile, or probe range of a
+// photon-number tile) is cut into units of equal length KC, chosen so that
+// the whole contraction has about four units per SM and column block.
+// Cuts the reduction range of every tile into work units of equal length.
+//   st/en: per-tile [start, end) of the reduction range (empty if equal)
+//   align: unit boundaries are multiples of `align` relative to 0 when
+//          `aligned_start` (start rounded down, end rounded up), else relative
+//          to the tile's start
+static cudaError_t make_schedule(Plan &p, Schedule &S, const std::vector<int64_t> &st,
+                                 const std::vector<int64_t> &en, int align, size_t part_elem_bytes,
+                                 int64_t *max_ctas)
+{
+    const int tiles = int(st.size());
+    const int bn = band_bn(p.N);
+    const int64_t ncol = (p.N + bn - 1) / bn;
+    int64_t W = 0;
+    for (int t = 0; t < tiles; ++t) W += en[t] - st[t];
+    const int64_t target = std::max<int64_t>(1, 4 * int64_t(p.num_sms) / ncol);
+    int64_t kc = std::max<int64_t>(4 * int64_t(align), (W + target - 1) / target);
+    kc = ((kc + align - 1) / align) * align;
+    std::vector<WorkUnit> units;
+    std::vector<int32_t> first(tiles, 0), nsplit(tiles, 1);
+    int64_t slots = 0;
+    for (int t = 0; t < tiles; ++t) {
+        const int64_t len = en[t] - st[t];
+        const int64_t n = len > 0 ? (len + kc - 1) / kc : 1;
+        nsplit[t] = int32_t(n);
+        if (n > 1) { first[t] = int32_t(slots); slots += n; }
+        for (int64_t c = 0; c < n; ++c) {
+            WorkUnit u;
+            u.tile = t;
+            u.chunk = int32_t(c);
+            u.k0 = int32_t(st[t] + c * kc);
+            u.k1 = int32_t(std::min<int64_t>(st[t] + (c + 1) * kc, en[t]));
+            if (len <= 0) u.k0 = u.k1 = 0;
+            units.push_back(u);
+        }
+    }
+    cudaError_t e;
+    S.n_units = int(units.size());
+    if ((e = dalloc(&S.units, int64_t(units.size())))) return e;
+    if ((e = dalloc(&S.tile_first, tiles))) return e;
+    if ((e = dalloc(&S.tile_nsplit, tiles))) return e;
+    if ((e = dalloc(&S.counters, tiles * ncol))) return e;
+    if ((e = cudaMalloc(&S.part, std::max<int64_t>(1, slots * ncol) * TILE_R * bn * part_elem_bytes))) return e;
+    if ((e = cudaMemcpy(S.units, units.data(), sizeof(WorkUnit) * units.size(), cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(S.tile_first, first.data(), sizeof(int32_t) * tiles, cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(S.tile_nsplit, nsplit.data(), sizeof(int32_t) * tiles, cudaMemcpyHostToDevice)) ||
+        (e = cudaMemset(S.counters, 0, sizeof(unsigned) * tiles * ncol)))
+        return e;
+    *max_ctas = std::max<int64_t>(*max_ctas, int64_t(units.size()) * ncol);
+    return cudaSuccess;
+}
+
+// Work-unit schedules of the band contractions (split-K): the reduction
+// range of every tile (union band of a probe tile, or probe range of a
+// photon-number tile) is cut into units of equal length, about four units per
+// SM and column block for the whole contraction.
+static cudaError_t build_schedules(Plan &p, bool tensor_cores)
+{
+    std::vector<int32_t> klo(p.fwd_tiles), khi(p.fwd_tiles), dlo(p.adj_tiles), dhi(p.adj_tiles);
+    cudaError_t e;
+    if ((e = cudaMemcpy(klo.data(), p.fwd_klo, sizeof(int32_t) * klo.size(), cudaMemcpyDeviceToHost)) ||
+        (e = cudaMemcpy(khi.data(), p.fwd_khi, sizeof(int32_t) * khi.size(), cudaMemcpyDeviceToHost)) ||
+        (e = cudaMemcpy(dlo.data(), p.adj_dlo, sizeof(int32_t) * dlo.size(), cudaMemcpyDeviceToHost)) ||
+        (e = cudaMemcpy(dhi.data(), p.adj_dhi, sizeof(int32_t) * dhi.size(), cudaMemcpyDeviceToHost)))
+        return e;
+    int64_t max_ctas = 0;
+    auto ranges = [&](bool fwd, int align_start, int align_end, std::vector<int64_t> &st,
+                      std::vector<int64_t> &en) {
+        const int tiles = fwd ? p.fwd_tiles : p.adj_tiles;
+        st.assign(tiles, 0);
+        en.assign(tiles, 0);
+        for (int t = 0; t < tiles; ++t) {
+            const int64_t a = fwd ? klo[t] : dlo[t], b = fwd ? khi[t] : dhi[t];
+            if (a > b) continue;
+            st[t] = (a / align_start) * align_start;
+            en[t] = ((b + 1 + align_end - 1) / align_end) * align_end;
+        }
+    };
+    for (int dir = 0; dir < 2; ++dir) {
+        for (int dbl = 0; dbl < 2; ++dbl) {
+            const int BK = dbl ? 16 : 32;
+            const bool fwd = dir == 0;
+            std::vector<int64_t> st, en;
+            // forward: K steps aligned to BK from 0; adjoint: probe ranges as they are
+            ranges(fwd, fwd ? BK : 1, fwd ? BK : 1, st, en);
+            if ((e = make_schedule(p, p.sched[dir][dbl], st, en, BK,
+                                   dbl ? sizeof(double) : sizeof(float), &max_ctas)))
+                return e;
+        }
+    }
+    if (tensor_cores) {
+        // tensor-core tiles reduce in slices of 64 aligned to 64 (16-byte,
+        // 128-byte-row loads from the zero-padded transposed copies)
+        for (int dir = 0; dir < 2; ++dir) {
+            std::vector<int64_t> st, en;
+            ranges(dir == 0, 64, 64, st, en);
+            if ((e = make_schedule(p, p.sched_tc[dir], st, en, 64, sizeof(float), &max_ctas)))
+                return e;
+        }
+        const int64_t npad = ((p.N + 127) / 128) * 128;
+        p.ut_pitch = ((p.M + 63) / 64) * 64;
+        p.ot_pitch = ((p.D + 63) / 64) * 64;
+        const size_t ub = sizeof(__nv_bfloat16) * size_t(npad * p.ut_pitch);
+        const size_t ob = sizeof(__nv_bfloat16) * size_t(npad * p.ot_pitch);
+        if ((e = cudaMalloc(&p.ut_hi, ub)) || (e = cudaMalloc(&p.ut_lo, ub)) ||
+            (e = cudaMalloc(&p.ot_hi, ob)) || (e = cudaMalloc(&p.ot_lo, ob)))
+            return e;
+        if ((e = cudaMemset(p.ut_hi, 0, ub)) || (e = cudaMemset(p.ut_lo, 0, ub)) ||
+            (e = cudaMemset(p.ot_hi, 0, ob)) || (e = cudaMemset(p.ot_lo, 0, ob)))
+            return e;
+    }
+    p.max_partials = std::max<int64_t>(p.max_partials, max_ctas);
+    return cudaSuccess;
 }
 
 // R = F Theta - P in double, f = ||R||^2 + g(Theta) (Eq. min + Eq. regul).
@@ -168,7 +299,8 @@ tomo_status tomo_plan(tomo_plan_t *out, const tomo_desc *d)
     if (!d->lambda) return fail(TOMO_EINVAL, "lambda is NULL");
     if (!std::isfinite(d->gamma) || d->gamma < 0.0) return fail(TOMO_EINVAL, "gamma must be finite and >= 0");
     if (!std::isfinite(d->band_k)) return fail(TOMO_EINVAL, "band_k must be finite");
-    if (d->precision != TOMO_PREC_FP64 && d->precision != TOMO_PREC_FP32)
+    if (d->precision != TOMO_PREC_FP64 && d->precision != TOMO_PREC_FP32 &&
+        d->precision != TOMO_PREC_MIXED && d->precision != TOMO_PREC_TC)
         return fail(TOMO_EINVAL, "unknown precision %d", d->precision);
     if (d->flags != 0) return fail(TOMO_EINVAL, "flags must be 0");
     for (int64_t k = 0; k < d->D; ++k) {
@@ -205,20 +337,17 @@ tomo_status tomo_plan(tomo_plan_t *out, const tomo_desc *d)
         p->own_stream = true;
     }
     const int64_t M = p->M, N = p->N, D = p->D, MN = M * N, DN = D * N;
-    p->fwd_tiles = int((D + FWD_BD - 1) / FWD_BD);
-    p->adj_tiles = int((M + ADJ_BI - 1) / ADJ_BI);
-    const int64_t ncol32 = (N + 31) / 32;
-    int64_t mp = int64_t(p->num_sms) * 8;
-    if (int64_t(p->fwd_tiles) * ncol32 > mp) mp = int64_t(p->fwd_tiles) * ncol32;
-    if (int64_t(p->adj_tiles) * ncol32 > mp) mp = int64_t(p->adj_tiles) * ncol32;
-    p->max_partials = mp;
+    p->fwd_tiles = int((D + TILE_R - 1) / TILE_R);
+    p->adj_tiles = int((M + TILE_R - 1) / TILE_R);
+    p->max_partials = int64_t(p->num_sms) * 8;  // row kernels; raised by the schedules
 
     PLAN_TRY(dalloc(&p->lam, D));
     PLAN_TRY(dalloc(&p->lo, D));
     PLAN_TRY(dalloc(&p->hi, D));
     PLAN_TRY(dalloc(&p->aoff, D + 1));
     PLAN_TRY(dalloc(&p->ratio_inv, M + RUN + 1));
-    PLAN_TRY(dalloc(&p->ratio_inv_f, M + RUN + 1));
+    PLAN_TRY(dalloc(&p->ratio_inv_f2, M + RUN + 1));
+    PLAN_TRY(dalloc(&p->lam_f2, D));
     PLAN_TRY(dalloc(&p->fwd_klo, p->fwd_tiles));
     PLAN_TRY(dalloc(&p->fwd_khi, p->fwd_tiles));
     PLAN_TRY(dalloc(&p->adj_dlo, p->adj_tiles));
@@ -233,7 +362,6 @@ tomo_status tomo_plan(tomo_plan_t *out, const tomo_desc *d)
     PLAN_TRY(dalloc(&p->freem, MN));
     PLAN_TRY(dalloc(&p->var, MN));
     PLAN_TRY(dalloc(&p->mrow, M));
-    PLAN_TRY(dalloc(&p->partials, RED_SLOTS * p->max_partials));
     PLAN_TRY(dalloc(&p->sc, 1));
     PLAN_TRY(cudaMallocHost(reinterpret_cast<void **>(&p->sc_host), sizeof(DevScalars)));
     PLAN_TRY(cudaMallocHost(reinterpret_cast<void **>(&p->scratch_host), 64 * sizeof(double)));
@@ -243,6 +371,8 @@ tomo_status tomo_plan(tomo_plan_t *out, const tomo_desc *d)
     PLAN_TRY(launch_plan_tables(*p));
     PLAN_TRY(launch_hess_diag(*p));
     PLAN_TRY(cudaStreamSynchronize(p->stream));
+    PLAN_TRY(build_schedules(*p, hvp_on_tensor_cores(p->precision)));
+    PLAN_TRY(dalloc(&p->partials, RED_SLOTS * p->max_partials));
 #undef PLAN_TRY
     *out = reinterpret_cast<tomo_plan_t>(p);
     return TOMO_OK;
@@ -274,7 +404,7 @@ tomo_status tomo_objective(tomo_plan_t plan, const double *P, const double *Thet
     if (grad) {
         const bool gdev = is_device_pointer(grad);
         double *gd = gdev ? grad : p.G;
-        CUDA_TRY(launch_adjoint(p, p.precision, ADJ_GRAD, p.R, gd, Td, false));
+        CUDA_TRY(launch_adjoint(p, prec_gradient(p.precision), ADJ_GRAD, p.R, gd, Td, false));
         if (!gdev)
             CUDA_TRY(cudaMemcpyAsync(grad, gd, sizeof(double) * size_t(MN), cudaMemcpyDeviceToHost,
                                      p.stream));
@@ -316,11 +446,19 @@ struct ChunkEvents {
 static tomo_status cg_chunk(Plan &p, int stage, int count, ChunkEvents *evs)
 {
     const double *in = stage == 1 ? p.p : p.u;
+    const bool tc = hvp_on_tensor_cores(p.precision);
     for (int c = 0; c < count; ++c) {
         if (evs) CUDA_TRY(cudaEventRecord(evs->ev[c][0], p.stream));
-        CUDA_TRY(launch_forward(p, p.precision, FWD_STORE, in, p.O, nullptr, true));
-        if (evs) CUDA_TRY(cudaEventRecord(evs->ev[c][1], p.stream));
-        CUDA_TRY(launch_adjoint(p, p.precision, ADJ_HESS, p.O, p.q, in, true));
+        if (tc) {
+            // tensor cores: the whole Hessian product (forward + adjoint) is
+            // timed as the "forward" interval, the adjoint interval is empty
+            CUDA_TRY(launch_hvp_tc(p, in, p.q, true));
+            if (evs) CUDA_TRY(cudaEventRecord(evs->ev[c][1], p.stream));
+        } else {
+            CUDA_TRY(launch_forward(p, prec_products(p.precision), FWD_STORE, in, p.O, nullptr, true));
+            if (evs) CUDA_TRY(cudaEventRecord(evs->ev[c][1], p.stream));
+            CUDA_TRY(launch_adjoint(p, prec_products(p.precision), ADJ_HESS, p.O, p.q, in, true));
+        }
         if (evs) CUDA_TRY(cudaEventRecord(evs->ev[c][2], p.stream));
         CUDA_TRY(launch_cg_restrict(p, stage));
         CUDA_TRY(launch_cg_update_xr(p, stage));
@@ -348,7 +486,7 @@ static tomo_status line_search(Plan &p, int stage, const double *P, double f,
         ++*ls_count;
         CUDA_TRY(launch_trial(p, stage, alpha, delta));
         if (delta)
-            CUDA_TRY(launch_forward_gated_ls(p, p.precision, FWD_DELTA, p.s, p.Rt, p.R));
+            CUDA_TRY(launch_forward_gated_ls(p, prec_products(p.precision), FWD_DELTA, p.s, p.Rt, p.R));
         else
             CUDA_TRY(launch_forward_gated_ls(p, TOMO_PREC_FP64, FWD_RESID, p.trial, p.Rt, P));
         TOMO_TRY(read_scalars(p));
@@ -391,7 +529,7 @@ static tomo_status fit_impl(Plan &p, const double *P, const tomo_fit_opts &o, to
     rep.stop = 2;
     for (int k = 0; k < o.max_newton; ++k) {
         // gradient G = 2 F^T R + 2 gamma L Theta
-        CUDA_TRY(launch_adjoint(p, p.precision, ADJ_GRAD, p.R, p.G, p.Th, false));
+        CUDA_TRY(launch_adjoint(p, prec_gradient(p.precision), ADJ_GRAD, p.R, p.G, p.Th, false));
         if (stage == 1 && rep.iters_s1 >= o.max_stage1) stage = 2;
         CUDA_TRY(launch_setup1(p, stage, o.eps_bar));
         CUDA_TRY(launch_setup2(p, stage, o.max_cg));
@@ -508,6 +646,8 @@ tomo_status tomo_fit(tomo_plan_t plan, const double *P, double *Theta, const tom
     }
     tomo_status st = fit_impl(p, Pd, o, rep);
     if (st != TOMO_OK) return st;
+    if (p.sc_host->tc_err)
+        return fail(TOMO_ETIMEOUT, "a bounded tensor-core pipeline wait gave up");
     CUDA_TRY(cudaMemcpyAsync(Theta, p.Th, sizeof(double) * size_t(MN),
                              tdev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, p.stream));
     CUDA_TRY(cudaStreamSynchronize(p.stream));
@@ -521,7 +661,7 @@ tomo_status tomo_apply_F(tomo_plan_t plan, const double *X, double *O)
 {
     Plan *p = reinterpret_cast<Plan *>(plan);
     if (!p || !X || !O) return fail(TOMO_EINVAL, "NULL argument");
-    CUDA_TRY(launch_forward(*p, p->precision, FWD_STORE, X, O, nullptr, false));
+    CUDA_TRY(launch_forward(*p, prec_products(p->precision), FWD_STORE, X, O, nullptr, false));
     CUDA_TRY(cudaStreamSynchronize(p->stream));
     return TOMO_OK;
 }
@@ -530,7 +670,7 @@ tomo_status tomo_apply_Ft(tomo_plan_t plan, const double *Y, double *Z)
 {
     Plan *p = reinterpret_cast<Plan *>(plan);
     if (!p || !Y || !Z) return fail(TOMO_EINVAL, "NULL argument");
-    CUDA_TRY(launch_adjoint(*p, p->precision, ADJ_STORE, Y, Z, nullptr, false));
+    CUDA_TRY(launch_adjoint(*p, prec_products(p->precision), ADJ_STORE, Y, Z, nullptr, false));
     CUDA_TRY(cudaStreamSynchronize(p->stream));
     return TOMO_OK;
 }
@@ -539,8 +679,12 @@ tomo_status tomo_hvp(tomo_plan_t plan, const double *V, double *HV)
 {
     Plan *p = reinterpret_cast<Plan *>(plan);
     if (!p || !V || !HV) return fail(TOMO_EINVAL, "NULL argument");
-    CUDA_TRY(launch_forward(*p, p->precision, FWD_STORE, V, p->O, nullptr, false));
-    CUDA_TRY(launch_adjoint(*p, p->precision, ADJ_GRAD, p->O, HV, V, false));
+    if (hvp_on_tensor_cores(p->precision)) {
+        CUDA_TRY(launch_hvp_tc(*p, V, HV, false));
+    } else {
+        CUDA_TRY(launch_forward(*p, prec_products(p->precision), FWD_STORE, V, p->O, nullptr, false));
+        CUDA_TRY(launch_adjoint(*p, prec_products(p->precision), ADJ_GRAD, p->O, HV, V, false));
+    }
     CUDA_TRY(cudaStreamSynchronize(p->stream));
     return TOMO_OK;
 }

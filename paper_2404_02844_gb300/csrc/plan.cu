@@ -122,23 +122,36 @@ __global__ void k_anchors(int64_t D, const double *lam, const int32_t *lo, const
     }
 }
 
-__global__ void k_ratio_inv(int64_t n, double *r, float *rf)
+// 1/i in double and as a float pair hi + lo (hi = float(1/i), lo = float(1/i - hi)),
+// and lambda_d as a float pair, so that the float weight recurrence can form
+// lambda / (i + 1) to ~1e-14 before its single rounding (no systematic bias
+// from rounding lambda or 1/i to float).
+__global__ void k_ratio_inv(int64_t n, double *r, float2 *rf2)
 {
     const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
     if (i >= n) return;
     const double v = i == 0 ? 0.0 : 1.0 / double(i);
     r[i] = v;
-    rf[i] = float(v);
+    const float hi = float(v);
+    rf2[i] = make_float2(hi, float(v - double(hi)));
 }
 
-// Forward tile t covers probes [FWD_BD t, FWD_BD (t+1)): union of their bands.
+__global__ void k_lam_split(int64_t D, const double *lam, float2 *lam2)
+{
+    const int64_t d = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (d >= D) return;
+    const float hi = float(lam[d]);
+    lam2[d] = make_float2(hi, float(lam[d] - double(hi)));
+}
+
+// Forward tile t covers probes [TILE_R t, TILE_R (t+1)): union of their bands.
 __global__ void k_fwd_tiles(int64_t D, int tiles, const int32_t *lo, const int32_t *hi,
                             int32_t *klo, int32_t *khi)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= tiles) return;
     int32_t a = INT32_MAX, b = -1;
-    for (int64_t d = int64_t(t) * FWD_BD; d < D && d < int64_t(t + 1) * FWD_BD; ++d) {
+    for (int64_t d = int64_t(t) * TILE_R; d < D && d < int64_t(t + 1) * TILE_R; ++d) {
         if (lo[d] > hi[d]) continue;
         a = min(a, lo[d]);
         b = max(b, hi[d]);
@@ -148,7 +161,7 @@ __global__ void k_fwd_tiles(int64_t D, int tiles, const int32_t *lo, const int32
     khi[t] = b;
 }
 
-// Adjoint tile t covers photon numbers [ADJ_BI t, ADJ_BI (t+1)).  With probes
+// Adjoint tile t covers photon numbers [TILE_R t, TILE_R (t+1)).  With probes
 // sorted by intensity, lo_d and hi_d are non-decreasing in d, so the probes
 // whose band meets the tile form the range [first d with hi_d >= i0,
 // last d with lo_d <= i1] (binary searches).
@@ -157,8 +170,8 @@ __global__ void k_adj_tiles(int64_t D, int64_t M, int tiles, const int32_t *lo,
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= tiles) return;
-    const int64_t i0 = int64_t(t) * ADJ_BI;
-    int64_t i1 = i0 + ADJ_BI - 1;
+    const int64_t i0 = int64_t(t) * TILE_R;
+    int64_t i1 = i0 + TILE_R - 1;
     if (i1 > M - 1) i1 = M - 1;
     int64_t a = 0, b = D;  // first d with hi_d >= i0
     while (a < b) {
@@ -192,17 +205,20 @@ __device__ double weight_from_anchor_d(int64_t d, int64_t i, const double *lam,
     return v;
 }
 
-__device__ float weight_from_anchor_f(int64_t d, int64_t i, const double *lam,
+__device__ float weight_from_anchor_f(int64_t d, int64_t i, const float2 *lam2,
                                       const int32_t *lo, const int32_t *hi,
                                       const int64_t *aoff, const float *anc,
-                                      const float *rinv)
+                                      const float2 *rinv2)
 {
     if (i < lo[d] || i > hi[d]) return 0.0f;
     const int64_t a0 = int64_t(lo[d]) & ~int64_t(RUN - 1);
     const int64_t ir = i & ~int64_t(RUN - 1);
     float v = anc[aoff[d] + (ir - a0) / RUN];
-    const float x = float(lam[d]);
-    for (int64_t j = ir; j < i; ++j) v = v * (x * rinv[j + 1]);
+    const float2 x = lam2[d];
+    for (int64_t j = ir; j < i; ++j) {
+        const float2 r = rinv2[j + 1];
+        v = v * fmaf(x.x, r.x, fmaf(x.x, r.y, x.y * r.x));
+    }
     return v;
 }
 
@@ -215,7 +231,7 @@ __global__ void k_hess_diag(int64_t M, double gamma, const double *lam, const in
 {
     const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
     if (i >= M) return;
-    const int t = int(i / ADJ_BI);
+    const int t = int(i / TILE_R);
     double s = 0.0;
     for (int64_t d = dlo[t]; d <= dhi[t]; ++d) {
         const double f = weight_from_anchor_d(d, i, lam, lo, hi, aoff, anc, rinv);
@@ -227,9 +243,9 @@ __global__ void k_hess_diag(int64_t M, double gamma, const double *lam, const in
 
 __global__ void k_poisson_weights(int64_t count, const int64_t *dd, const int64_t *ii,
                                   int prec, int64_t D, int64_t M, const double *lam,
-                                  const int32_t *lo, const int32_t *hi, const int64_t *aoff,
-                                  const double *anc, const float *anc_f, const double *rinv,
-                                  const float *rinv_f, double *out)
+                                  const float2 *lam2, const int32_t *lo, const int32_t *hi,
+                                  const int64_t *aoff, const double *anc, const float *anc_f,
+                                  const double *rinv, const float2 *rinv_f2, double *out)
 {
     const int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
     if (k >= count) return;
@@ -237,7 +253,7 @@ __global__ void k_poisson_weights(int64_t count, const int64_t *dd, const int64_
     if (d < 0 || d >= D || i < 0 || i >= M) { out[k] = 0.0; return; }
     out[k] = prec == TOMO_PREC_FP64
                  ? weight_from_anchor_d(d, i, lam, lo, hi, aoff, anc, rinv)
-                 : double(weight_from_anchor_f(d, i, lam, lo, hi, aoff, anc_f, rinv_f));
+                 : double(weight_from_anchor_f(d, i, lam2, lo, hi, aoff, anc_f, rinv_f2));
 }
 
 static inline unsigned blocks_for(int64_t n, int t) { return unsigned((n + t - 1) / t); }
@@ -270,7 +286,9 @@ cudaError_t launch_plan_tables(Plan &p)
                                                           p.anchor, p.anchor_f);
     count_launch();
     const int64_t nr = p.M + RUN + 1;
-    k_ratio_inv<<<blocks_for(nr, 256), 256, 0, p.stream>>>(nr, p.ratio_inv, p.ratio_inv_f);
+    k_ratio_inv<<<blocks_for(nr, 256), 256, 0, p.stream>>>(nr, p.ratio_inv, p.ratio_inv_f2);
+    count_launch();
+    k_lam_split<<<blocks_for(p.D, 256), 256, 0, p.stream>>>(p.D, p.lam, p.lam_f2);
     count_launch();
     k_fwd_tiles<<<blocks_for(p.fwd_tiles, 128), 128, 0, p.stream>>>(p.D, p.fwd_tiles, p.lo,
                                                                     p.hi, p.fwd_klo, p.fwd_khi);
@@ -294,8 +312,8 @@ cudaError_t launch_poisson_weights(Plan &p, const int64_t *d, const int64_t *i, 
 {
     if (count <= 0) return cudaSuccess;
     k_poisson_weights<<<blocks_for(count, 128), 128, 0, p.stream>>>(
-        count, d, i, p.precision, p.D, p.M, p.lam, p.lo, p.hi, p.aoff, p.anchor, p.anchor_f,
-        p.ratio_inv, p.ratio_inv_f, out);
+        count, d, i, prec_products(p.precision), p.D, p.M, p.lam, p.lam_f2, p.lo, p.hi, p.aoff,
+        p.anchor, p.anchor_f, p.ratio_inv, p.ratio_inv_f2, out);
     count_launch();
     return cudaGetLastError();
 }

@@ -1,0 +1,443 @@
+// tc_band.cu -- the band contractions of the CG Hessian products on the
+// 5th-generation tensor cores (tcgen05.mma, kind::f16).
+//
+//   forward  O = F U   : tile of 128 probes x BN outcomes, reduced over the
+//                        union band of the tile's probes (photon numbers);
+//   adjoint  Z = F^T O : tile of 128 photon numbers x BN outcomes, reduced
+//                        over the probes whose band meets the tile;
+//   HVP = 2 F^T (F u) + 2 gamma L u (Table ops, Hessian products).
+//
+// Operands are bf16 in shared memory, K-major, 128-byte swizzled; the
+// accumulator is f32 in tensor memory.  Precision is recovered by splitting
+// every operand into hi + lo bf16 parts and accumulating hi*hi + hi*lo +
+// lo*hi (three MMAs per K slice, ~16 significant bits; the lo*lo term is
+// below f32 rounding of the accumulator's scale).  The weights F are generated
+// by all 256 threads straight into the swizzled A tile (runs of 8 photon
+// numbers from the log-space anchors, exact ratio recurrence in float); the
+// vector operand comes from a transposed bf16 hi/lo copy (rows = outcomes,
+// contiguous along the reduction index) so that one 16-byte load is one
+// swizzle chunk.  A single thread issues the MMAs of a stage and commits them
+// to the stage's mbarrier while the other threads already produce the next
+// stage (two stages).  The reduction range of every tile is cut into work
+// units (split-K, planned on the host); units of one tile write f32 partial
+// tiles and the last one to finish sums them in unit order.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "tc_ptx.cuh"
+#include "tomo_device.cuh"
+#include "tomo_internal.cuh"
+
+namespace tomo {
+
+constexpr int TC_BK = 64;       // reduction slice per stage (one 128-byte bf16 row)
+constexpr int TC_STAGES = 2;
+constexpr int TC_THREADS = 256;
+constexpr uint32_t TC_WAIT_LIMIT = 1u << 24;
+
+template <int BN, int SPLIT>
+struct TcLayout {
+    static constexpr int NPART = SPLIT == 3 ? 2 : 1;                 // hi (+ lo)
+    static constexpr int A_BYTES = TILE_R * TC_BK * 2;               // 16 KB
+    static constexpr int B_BYTES = BN * TC_BK * 2;
+    static constexpr int STAGE_BYTES = NPART * (A_BYTES + B_BYTES);
+    static constexpr int STAGING_BYTES = (TC_THREADS / 8) * 8 * 9 * 4;  // 8x8 transposes (+pad)
+    static constexpr int CTRL_BYTES = 64;
+    static constexpr int TOTAL = 1024 + TC_STAGES * STAGE_BYTES + STAGING_BYTES + CTRL_BYTES;
+    static constexpr int TMEM_COLS = BN < 32 ? 32 : BN;
+};
+
+struct TcArgs {
+    int64_t M, N, D;
+    const float2 *lam2;
+    const int32_t *lo, *hi;
+    const int64_t *aoff;
+    const float *anchor;
+    const float2 *rinv2;
+    const WorkUnit *units;
+    const int32_t *tile_first;
+    const int32_t *tile_nsplit;
+    unsigned int *counters;
+    float *part;
+    const int32_t *gate;
+    int32_t *err;                 // set to 1 if a bounded wait gave up
+    // operand B: transposed bf16 hi/lo copy, rows = outcomes, pitch bpitch
+    const __nv_bfloat16 *b_hi, *b_lo;
+    int64_t bpitch;
+    // forward output: transposed bf16 hi/lo copy of O (pitch opitch)
+    __nv_bfloat16 *o_hi, *o_lo;
+    int64_t opitch;
+    // adjoint output: q = 2 Z + 2 gamma L u (double, M x N)
+    double *q;
+    const double *u;
+    double gamma;
+};
+
+// Float weights of the run of 8 photon numbers i_r.. of probe d (zero outside
+// the band); same recurrence as the float SIMT contraction.
+__device__ __forceinline__ void tc_gen_run(const TcArgs &a, int64_t d, int64_t i_r, float (&v8)[RUN])
+{
+#pragma unroll
+    for (int t = 0; t < RUN; ++t) v8[t] = 0.f;
+    if (d >= a.D) return;
+    const int64_t lo = a.lo[d], hi = a.hi[d];
+    if (i_r + RUN - 1 < lo || i_r > hi) return;
+    const int64_t a0 = lo & ~int64_t(RUN - 1);
+    float v = a.anchor[a.aoff[d] + (i_r - a0) / RUN];
+    const float2 lam = a.lam2[d];
+#pragma unroll
+    for (int t = 0; t < RUN; ++t) {
+        const int64_t i = i_r + t;
+        v8[t] = (i >= lo && i <= hi) ? v : 0.f;
+        const float2 r = a.rinv2[i + 1];
+        v = v * fmaf(lam.x, r.x, fmaf(lam.x, r.y, lam.y * r.x));
+    }
+}
+
+// Packs 8 floats into hi and lo bf16 chunks (hi = rn(v), lo = rn(v - hi)).
+__device__ __forceinline__ void split_pack(const float (&v)[8], uint4 &hi, uint4 &lo)
+{
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const __nv_bfloat16 h0 = __float2bfloat16_rn(v[2 * k]);
+        const __nv_bfloat16 h1 = __float2bfloat16_rn(v[2 * k + 1]);
+        const __nv_bfloat16 l0 = __float2bfloat16_rn(v[2 * k] - __bfloat162float(h0));
+        const __nv_bfloat16 l1 = __float2bfloat16_rn(v[2 * k + 1] - __bfloat162float(h1));
+        h[k] = uint32_t(__bfloat16_as_ushort(h0)) | (uint32_t(__bfloat16_as_ushort(h1)) << 16);
+        l[k] = uint32_t(__bfloat16_as_ushort(l0)) | (uint32_t(__bfloat16_as_ushort(l1)) << 16);
+    }
+    hi = make_uint4(h[0], h[1], h[2], h[3]);
+    lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+template <int BN, int SPLIT, bool FWD>
+__global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(TcArgs a)
+{
+    using L = TcLayout<BN, SPLIT>;
+    if (a.gate && *a.gate == 0) return;
+
+    extern __shared__ unsigned char tc_raw[];
+    const uint32_t raw_u32 = tc::smem_u32(tc_raw);
+    unsigned char *sm = tc_raw + (((raw_u32 + 1023u) & ~1023u) - raw_u32);
+    float *staging = reinterpret_cast<float *>(sm + TC_STAGES * L::STAGE_BYTES);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + TC_STAGES * L::STAGE_BYTES + L::STAGING_BYTES);
+    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + TC_STAGES);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const WorkUnit wu = a.units[blockIdx.x];
+    const int tile = wu.tile;
+    const int64_t r0 = int64_t(tile) * TILE_R;
+    const int64_t n0 = int64_t(blockIdx.y) * BN;
+
+    if (warp == 0) {
+        tc::tmem_alloc(tmem_holder, L::TMEM_COLS);
+        tc::tmem_relinquish();
+    }
+    if (tid == 0) {
+        for (int s = 0; s < TC_STAGES; ++s) tc::mbar_init(&bars[s], 1);
+        tc::mbar_fence_init();
+    }
+    tc::tc_fence_before_sync();
+    __syncthreads();
+    tc::tc_fence_after_sync();
+    const uint32_t tmem = *tmem_holder;
+
+    constexpr uint32_t IDESC = tc::idesc_bf16_f32(TILE_R, BN);
+    const int nsteps = (wu.k1 - wu.k0) / TC_BK;
+    bool ok = true;
+
+    for (int s = 0; s < nsteps; ++s) {
+        const int st = s % TC_STAGES;
+        unsigned char *stage = sm + st * L::STAGE_BYTES;
+        unsigned char *A_hi = stage;
+        unsigned char *A_lo = stage + L::A_BYTES;                       // SPLIT == 3 only
+        unsigned char *B_hi = stage + L::NPART * L::A_BYTES;
+        unsigned char *B_lo = B_hi + L::B_BYTES;                        // SPLIT == 3 only
+        if (s >= TC_STAGES) {
+            // the MMAs issued TC_STAGES steps ago read this stage
+            if (!tc::mbar_wait_bounded(&bars[st], uint32_t((s / TC_STAGES) - 1) & 1u, TC_WAIT_LIMIT))
+                ok = false;
+        }
+        const int64_t k0 = int64_t(wu.k0) + int64_t(s) * TC_BK;
+
+        // ---- operand A: Poisson weights ----
+#pragma unroll
+        for (int q = 0; q < (TILE_R * TC_BK / RUN) / TC_THREADS; ++q) {
+            const int run = tid + q * TC_THREADS;
+            float v8[RUN];
+            int row, chunk;
+            if (FWD) {
+                // row = probe r0 + r, chunk = photon numbers k0 + 8 j .. + 7
+                row = run % TILE_R;
+                chunk = run / TILE_R;
+                tc_gen_run(a, r0 + row, k0 + int64_t(chunk) * RUN, v8);
+            } else {
+                // 8 x 8 block (8 probes x 8 photon numbers) per group of 8
+                // lanes, transposed through shared memory so that one lane
+                // holds 8 consecutive probes of one photon number
+                const int g = run >> 3, t = run & 7;
+                const int pb = g % (TILE_R / 8), kb = g / (TILE_R / 8);
+                float w8[RUN];
+                tc_gen_run(a, k0 + kb * 8 + t, r0 + pb * 8, w8);
+                float *stg = staging + ((tid >> 3) * 8) * 9;
+#pragma unroll
+                for (int j = 0; j < RUN; ++j) stg[t * 9 + j] = w8[j];
+                __syncwarp();
+#pragma unroll
+                for (int j = 0; j < RUN; ++j) v8[j] = stg[j * 9 + t];
+                __syncwarp();
+                row = pb * 8 + t;
+                chunk = kb;
+            }
+            uint4 hi, lo;
+            split_pack(v8, hi, lo);
+            *reinterpret_cast<uint4 *>(A_hi + tc::sw128_chunk(row, chunk)) = hi;
+            if (SPLIT == 3) *reinterpret_cast<uint4 *>(A_lo + tc::sw128_chunk(row, chunk)) = lo;
+        }
+        // ---- operand B: transposed bf16 copy of the vector ----
+        constexpr int BCH = BN * (TC_BK / 8);          // 16-byte chunks per part
+#pragma unroll
+        for (int q = 0; q < (L::NPART * BCH + TC_THREADS - 1) / TC_THREADS; ++q) {
+            const int c = tid + q * TC_THREADS;
+            if (c < L::NPART * BCH) {
+                const int part = c / BCH, cc = c % BCH;
+                const int n = cc / (TC_BK / 8), j = cc % (TC_BK / 8);
+                const __nv_bfloat16 *src = (part == 0 ? a.b_hi : a.b_lo) + (n0 + n) * a.bpitch + k0 + j * 8;
+                const uint4 val = *reinterpret_cast<const uint4 *>(src);
+                *reinterpret_cast<uint4 *>((part == 0 ? B_hi : B_lo) + tc::sw128_chunk(n, j)) = val;
+            }
+        }
+        tc::fence_proxy_async_smem();
+        tc::tc_fence_before_sync();
+        __syncthreads();
+        if (tid == 0) {
+            tc::tc_fence_after_sync();
+            const uint32_t a_hi = tc::smem_u32(A_hi), a_lo = tc::smem_u32(A_lo);
+            const uint32_t b_hi = tc::smem_u32(B_hi), b_lo = tc::smem_u32(B_lo);
+#pragma unroll
+            for (int kk = 0; kk < TC_BK / 16; ++kk) {
+                const uint32_t off = kk * 32;   // 16 bf16 per MMA
+                const uint32_t acc0 = (s > 0 || kk > 0) ? 1u : 0u;
+                tc::mma_bf16(tmem, tc::desc_kmajor_sw128(a_hi + off), tc::desc_kmajor_sw128(b_hi + off), IDESC, acc0);
+                if (SPLIT == 3) {
+                    tc::mma_bf16(tmem, tc::desc_kmajor_sw128(a_hi + off), tc::desc_kmajor_sw128(b_lo + off), IDESC, 1u);
+                    tc::mma_bf16(tmem, tc::desc_kmajor_sw128(a_lo + off), tc::desc_kmajor_sw128(b_hi + off), IDESC, 1u);
+                }
+            }
+            tc::mma_commit(&bars[st]);
+        }
+    }
+    if (nsteps > 0) {
+        const int s = nsteps - 1;
+        if (!tc::mbar_wait_bounded(&bars[s % TC_STAGES], uint32_t(s / TC_STAGES) & 1u, TC_WAIT_LIMIT))
+            ok = false;
+    }
+    tc::tc_fence_after_sync();
+
+    // ---- epilogue: tensor memory -> registers ----
+    // warp w reads TMEM lanes 32 (w % 4) .. + 31 (tile rows) and the column
+    // half w / 4 (BN >= 64) or all columns (BN == 32, warps 0-3 only)
+    const int lg = warp & 3;
+    const int row = lg * 32 + lane;
+    constexpr int COLS_PER_WARP = BN >= 64 ? BN / 2 : BN;
+    const int col0 = BN >= 64 ? (warp >> 2) * COLS_PER_WARP : 0;
+    const bool active = BN >= 64 || warp < 4;
+    const int nsplit = a.tile_nsplit[tile];
+    const int ncb = gridDim.y;
+    const int64_t tile_elems = int64_t(TILE_R) * BN;
+    __shared__ int last;
+
+    float acc[COLS_PER_WARP];
+    if (active) {
+#pragma unroll
+        for (int c = 0; c < COLS_PER_WARP; c += 32) {
+            uint32_t r[32];
+            if (nsteps > 0) {
+                tc::tmem_ld_32x32b_x32(tmem + (uint32_t(lg * 32) << 16) + uint32_t(col0 + c), r);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 32; ++k) r[k] = 0u;
+            }
+#pragma unroll
+            for (int k = 0; k < 32; ++k) acc[c + k] = __uint_as_float(r[k]);
+        }
+    }
+    bool owner = true;
+    if (nsplit > 1) {
+        float *mine = a.part + (int64_t(a.tile_first[tile] + wu.chunk) * ncb + blockIdx.y) * tile_elems;
+        if (active) {
+#pragma unroll
+            for (int c = 0; c < COLS_PER_WARP; c += 4)
+                *reinterpret_cast<float4 *>(&mine[row * BN + col0 + c]) =
+                    make_float4(acc[c], acc[c + 1], acc[c + 2], acc[c + 3]);
+        }
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) {
+            unsigned *ctr = &a.counters[int64_t(tile) * ncb + blockIdx.y];
+            last = atomicAdd(ctr, 1u) == unsigned(nsplit - 1);
+            if (last) *ctr = 0u;
+        }
+        __syncthreads();
+        owner = last != 0;
+        if (owner && active) {
+            __threadfence();
+#pragma unroll
+            for (int c = 0; c < COLS_PER_WARP; ++c) acc[c] = 0.f;
+            for (int sidx = 0; sidx < nsplit; ++sidx) {
+                const float *src = a.part + (int64_t(a.tile_first[tile] + sidx) * ncb + blockIdx.y) * tile_elems;
+#pragma unroll
+                for (int c = 0; c < COLS_PER_WARP; c += 4) {
+                    const float4 t = __ldcg(reinterpret_cast<const float4 *>(&src[row * BN + col0 + c]));
+                    acc[c] += t.x; acc[c + 1] += t.y; acc[c + 2] += t.z; acc[c + 3] += t.w;
+                }
+            }
+        }
+    }
+    if (owner && active) {
+        const int64_t grow = r0 + row;
+        if (FWD) {
+            // O^T hi/lo copies for the adjoint's operand B
+            if (grow < a.D) {
+#pragma unroll
+                for (int c = 0; c < COLS_PER_WARP; ++c) {
+                    const int64_t n = n0 + col0 + c;
+                    if (n < a.N) {
+                        const __nv_bfloat16 h = __float2bfloat16_rn(acc[c]);
+                        a.o_hi[n * a.opitch + grow] = h;
+                        a.o_lo[n * a.opitch + grow] = __float2bfloat16_rn(acc[c] - __bfloat162float(h));
+                    }
+                }
+            }
+        } else if (grow < a.M) {
+            const double g2 = 2.0 * a.gamma;
+#pragma unroll
+            for (int c = 0; c < COLS_PER_WARP; ++c) {
+                const int64_t n = n0 + col0 + c;
+                if (n < a.N) {
+                    const int64_t k = grow * a.N + n;
+                    double lx = 0.0;
+                    if (g2 != 0.0) {
+                        const double xi = a.u[k];
+                        if (grow < a.M - 1) lx += xi - a.u[k + a.N];
+                        if (grow > 0) lx += xi - a.u[k - a.N];
+                    }
+                    a.q[k] = 2.0 * double(acc[c]) + g2 * lx;
+                }
+            }
+        }
+    }
+    tc::tc_fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, L::TMEM_COLS);
+    if (!ok && tid == 0) atomicExch(a.err, 1);
+}
+
+// ----------------------------------------------------------------------------
+// u (double, M x N row-major) -> transposed bf16 hi/lo copies (rows = outcomes,
+// pitch = padded M), through a 32 x 32 shared-memory tile so that both the
+// reads and the writes are coalesced.  Gated like the CG kernels.
+// ----------------------------------------------------------------------------
+__global__ void k_transpose_split(const int32_t *gate, int64_t M, int64_t N, const double *u,
+                                  __nv_bfloat16 *t_hi, __nv_bfloat16 *t_lo, int64_t pitch)
+{
+    if (gate && *gate == 0) return;
+    __shared__ double tile[32][33];
+    const int64_t i0 = int64_t(blockIdx.x) * 32, nb = int64_t(blockIdx.y) * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int64_t i = i0 + r, n = nb + threadIdx.x;
+        tile[r][threadIdx.x] = (i < M && n < N) ? u[i * N + n] : 0.0;
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int64_t n = nb + r, i = i0 + threadIdx.x;
+        if (n < N && i < M) {
+            // hi = bf16(u), lo = bf16(u - hi)
+            const double v = tile[threadIdx.x][r];
+            const __nv_bfloat16 h = __float2bfloat16_rn(float(v));
+            t_hi[n * pitch + i] = h;
+            t_lo[n * pitch + i] = __float2bfloat16_rn(float(v - double(__bfloat162float(h))));
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------
+// launchers
+// ----------------------------------------------------------------------------
+template <int BN, int SPLIT, bool FWD>
+static cudaError_t launch_tc_t(Plan &p, const TcArgs &a)
+{
+    auto kern = k_band_tc<BN, SPLIT, FWD>;
+    const int smem = TcLayout<BN, SPLIT>::TOTAL;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    const Schedule &S = p.sched_tc[FWD ? 0 : 1];
+    dim3 grid(unsigned(S.n_units), unsigned((p.N + BN - 1) / BN));
+    kern<<<grid, TC_THREADS, smem, p.stream>>>(a);
+    count_launch();
+    return cudaGetLastError();
+}
+
+template <bool FWD>
+static cudaError_t launch_tc(Plan &p, const TcArgs &a)
+{
+    switch (band_bn(p.N)) {
+    case 128: return launch_tc_t<128, 3, FWD>(p, a);
+    case 64: return launch_tc_t<64, 3, FWD>(p, a);
+    default: return launch_tc_t<32, 3, FWD>(p, a);
+    }
+}
+
+static TcArgs tc_args(Plan &p, bool fwd, const int32_t *gate)
+{
+    TcArgs a;
+    a.M = p.M; a.N = p.N; a.D = p.D;
+    a.lam2 = p.lam_f2; a.lo = p.lo; a.hi = p.hi; a.aoff = p.aoff;
+    a.anchor = p.anchor_f; a.rinv2 = p.ratio_inv_f2;
+    const Schedule &S = p.sched_tc[fwd ? 0 : 1];
+    a.units = S.units; a.tile_first = S.tile_first; a.tile_nsplit = S.tile_nsplit;
+    a.counters = S.counters; a.part = reinterpret_cast<float *>(S.part);
+    a.gate = gate;
+    a.err = &p.sc->tc_err;
+    a.b_hi = fwd ? p.ut_hi : p.ot_hi;
+    a.b_lo = fwd ? p.ut_lo : p.ot_lo;
+    a.bpitch = fwd ? p.ut_pitch : p.ot_pitch;
+    a.o_hi = p.ot_hi; a.o_lo = p.ot_lo; a.opitch = p.ot_pitch;
+    a.q = nullptr; a.u = nullptr;
+    a.gamma = p.gamma;
+    return a;
+}
+
+// HV = 2 F^T (F V) + 2 gamma L V on the tensor cores (three launches: the
+// transposed split copy of V, the forward tile product, the adjoint tile
+// product with the smoothness term).
+cudaError_t launch_hvp_tc(Plan &p, const double *V, double *HV, bool gated)
+{
+    const int32_t *gate = gated ? &p.sc->cg_active : nullptr;
+    dim3 tb(32, 8), tg(unsigned((p.M + 31) / 32), unsigned((p.N + 31) / 32));
+    k_transpose_split<<<tg, tb, 0, p.stream>>>(gate, p.M, p.N, V, p.ut_hi, p.ut_lo, p.ut_pitch);
+    count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    TcArgs f = tc_args(p, true, gate);
+    if ((e = launch_tc<true>(p, f)) != cudaSuccess) return e;
+    TcArgs b = tc_args(p, false, gate);
+    b.q = HV;
+    b.u = V;
+    return launch_tc<false>(p, b);
+}
+
+size_t tc_smem_bytes(int bn)
+{
+    if (bn == 128) return TcLayout<128, 3>::TOTAL;
+    if (bn == 64) return TcLayout<64, 3>::TOTAL;
+    return TcLayout<32, 3>::TOTAL;
+}
+
+}  // namespace tomo

@@ -2,6 +2,7 @@
 // units of libtomo (plan kernels, band contractions, row kernels, host API).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -11,18 +12,16 @@ namespace tomo {
 
 // ---------------------------------------------------------------------------
 // Geometry of the band contraction tiles.
-//   Forward  O = F X : CTA tile of FWD_BD probes x BN columns, K steps of BK
-//                      photon numbers inside the tile's union band.
-//   Adjoint  Z = F^T Y : CTA tile of ADJ_BI photon numbers x BN columns,
-//                      steps of ADJ_BKD probes inside the tile's probe range.
-// Poisson weights are generated in runs of RUN consecutive photon numbers
-// from an anchor stored every RUN photon numbers (see plan.cu).
+//   Forward  O = F X   : tiles of TILE_R probes x BN columns, reduced over the
+//                        union band of the tile's probes (photon numbers).
+//   Adjoint  Z = F^T Y : tiles of TILE_R photon numbers x BN columns, reduced
+//                        over the probes whose band meets the tile.
+// The reduction range of every tile is cut into work units (split-K) planned
+// on the host.  Poisson weights are generated in runs of RUN consecutive
+// photon numbers from an anchor stored every RUN photon numbers (plan.cu).
 // ---------------------------------------------------------------------------
 constexpr int RUN = 8;
-constexpr int FWD_BD = 64;
-constexpr int FWD_BK = 32;
-constexpr int ADJ_BI = 64;
-constexpr int ADJ_BKD = 32;
+constexpr int TILE_R = 128;
 constexpr int GEMM_THREADS = 256;
 constexpr int ROW_WARPS = 8;              // warps per CTA in row kernels
 constexpr int MAX_N = 1024;               // outcomes supported by row kernels
@@ -39,11 +38,27 @@ struct DevScalars {
     int32_t use_grad_dir, pad1;
     // line search
     double alpha_ls, gts, reg, dres, f_trial;
-    int32_t neg, accept, ls_go, pad2;
+    int32_t neg, accept, ls_go, tc_err;
     // objective pieces
     double res2, regval, nonfinite;
     // counters for the last-block reductions (one per concurrent site)
     unsigned int ticket[4];
+};
+
+// One CTA of a band contraction: reduction range [k0, k1) of tile `tile`,
+// chunk index `chunk` among the tile's units.
+struct WorkUnit {
+    int32_t tile, chunk, k0, k1;
+};
+
+// Work-unit schedule of one contraction (direction x arithmetic type).
+struct Schedule {
+    WorkUnit *units;        // device, n_units
+    int32_t *tile_first;    // device, per tile: first partial slot
+    int32_t *tile_nsplit;   // device, per tile: number of units
+    unsigned int *counters; // device, per (tile, column block)
+    void *part;             // device partial tiles
+    int n_units;
 };
 
 struct Plan {
@@ -61,13 +76,19 @@ struct Plan {
     int64_t *aoff;     // D + 1 offsets into the anchor table
     double *anchor;    // F_{d, a0_d + RUN j}, a0_d = lo_d rounded down to RUN
     float *anchor_f;   // same, rounded to float
-    double *ratio_inv; // M + 1: 1/(i) for i >= 1 (ratio_inv[0] unused)
-    float *ratio_inv_f;
+    double *ratio_inv; // M + RUN + 1: 1/i for i >= 1 (ratio_inv[0] unused)
+    float2 *ratio_inv_f2;  // 1/i as an unevaluated float sum hi + lo
+    float2 *lam_f2;        // lambda_d as hi + lo floats
     int32_t *fwd_klo, *fwd_khi;  // per forward tile (probes)
     int32_t *adj_dlo, *adj_dhi;  // per adjoint tile (photon numbers)
     double *h;         // M: Hessian diagonal
     int64_t n_anchor;
     int fwd_tiles, adj_tiles;
+    Schedule sched[2][2];      // [forward, adjoint][float, double]
+    Schedule sched_tc[2];      // tensor-core contractions [forward, adjoint]
+    // transposed bf16 hi/lo copies of the tensor-core operands
+    __nv_bfloat16 *ut_hi, *ut_lo, *ot_hi, *ot_lo;
+    int64_t ut_pitch, ot_pitch;
 
     // workspaces (device), M x N unless noted
     double *Th, *trial, *s, *G, *g, *x, *r, *z, *p, *u, *q, *dir;
@@ -121,6 +142,19 @@ cudaError_t launch_direction(Plan &p, int stage);
 cudaError_t launch_trial(Plan &p, int stage, double alpha, bool delta_mode);
 cudaError_t launch_set_grad_dir(Plan &p);
 cudaError_t launch_nonfinite_check(Plan &p, const double *x, int64_t n, int slot);
+
+int band_bn(int64_t N);
+template <typename T> size_t band_smem_bytes(int bn);
+
+// arithmetic of the CG Hessian products / line-search products, and of the
+// gradient, for a plan precision
+inline int prec_products(int precision) { return precision == TOMO_PREC_FP64 ? TOMO_PREC_FP64 : TOMO_PREC_FP32; }
+inline int prec_gradient(int precision) { return precision == TOMO_PREC_FP32 ? TOMO_PREC_FP32 : TOMO_PREC_FP64; }
+inline bool hvp_on_tensor_cores(int precision) { return precision == TOMO_PREC_TC; }
+
+// tc_band.cu
+cudaError_t launch_hvp_tc(Plan &p, const double *V, double *HV, bool gated);
+size_t tc_smem_bytes(int bn);
 
 // kernel launch accounting (all threads)
 void count_launch(int n = 1);

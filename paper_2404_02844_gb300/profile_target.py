@@ -1,0 +1,62 @@
+"""Profiling target: plans one synthetic workload and runs the solver for a
+fixed number of Newton iterations (a representative mix of every kernel of
+the hot path), for use under ncu:
+
+    python -m paper_2404_02844_gb300.profile_target --config c2 --precision fp32 --newton 3
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--config", default="c2", choices=["c1", "c2"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--newton", type=int, default=3)
+    ap.add_argument("--op", default="fit", choices=["fit", "hvp", "fwd", "adj"],
+                    help="fit: the solver; hvp/fwd/adj: --reps single products")
+    ap.add_argument("--reps", type=int, default=5)
+    args = ap.parse_args()
+
+    import torch
+
+    import paper_2404_02844_gb300 as tomo
+    import workloads
+    from paper_2404_02844_gb300 import build
+
+    build.build()
+    w = {"c1": workloads.config_c1, "c2": workloads.config_c2}[args.config]()
+    P = torch.from_numpy(w.P).cuda()
+    with tomo.Plan.from_workload(w, precision=args.precision) as pl:
+        if args.op != "fit":
+            g = torch.Generator(device="cuda").manual_seed(1)
+            X = torch.rand(w.M, w.N, dtype=torch.float64, device="cuda", generator=g)
+            Y = torch.rand(w.D, w.N, dtype=torch.float64, device="cuda", generator=g)
+            fn = {"hvp": lambda: pl.hvp(X), "fwd": lambda: pl.apply_F(X),
+                  "adj": lambda: pl.apply_Ft(Y)}[args.op]
+            t0 = time.perf_counter()
+            for _ in range(args.reps):
+                fn()
+            torch.cuda.synchronize()
+            print(f"{w.name} {args.precision}: {args.reps} x {args.op}, "
+                  f"{(time.perf_counter() - t0) / args.reps * 1e3:.3f} ms each")
+            return
+        t0 = time.perf_counter()
+        _, rep = pl.fit(P, max_newton=args.newton, eps_kkt=0.0)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+    print(f"{w.name} {args.precision}: {args.newton} Newton iterations, "
+          f"{rep['cg_total']} CG products, {rep['ls_total']} line-search trials, "
+          f"{rep['kernels']} kernels, {dt:.3f}s, f={rep['f']:.12e}")
+
+
+if __name__ == "__main__":
+    main()

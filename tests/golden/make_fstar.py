@@ -5,7 +5,9 @@ FP64 oracle only (no GPU code is imported):
 
 The oracle's solver (Algorithm 3) runs in chunks of Newton iterations, each
 chunk warm-started from the previous iterate (the first chunk is the plain
-two-stage start from Theta = 1/N, the following ones run stage 2).  After
+two-stage start from Theta = 1/N, the following ones run stage 2 with up to
+250 CG products per Newton step; the optimum of the strictly convex problem
+does not depend on the path).  After
 each chunk the Frank-Wolfe duality gap of the iterate bounds f - f* from
 above (convexity, see orc_fw_gap); the run stops once that bound is below
 1e-11 * f, so f* is known to 1e-11 relative without trusting the solver,
@@ -16,7 +18,10 @@ limited by rounding in G and is reported as it stands).
 Output tests/golden/fstar_<cfg>.json: f_star (the final objective, an upper
 bound), f_lower (f - FW gap, a lower bound), the KKT residual, iteration
 counts, sampled rows of Theta* and the change of those rows over the last
-chunk (theta_drift)."""
+chunk (theta_drift), and theta_tol: 10 x the largest difference, on the
+sampled rows, between Theta* and the oracle's iterate at KKT <= 1e-10 (a
+separate run from Theta = 1/N, the calibration of the Theta tolerance:
+Theta is poorly determined along the flat directions of the objective)."""
 import json
 import os
 import sys
@@ -34,7 +39,14 @@ CONFIGS = {"c1": workloads.config_c1, "c2": workloads.config_c2}
 REL = 1e-11
 
 
-def main(name: str, chunk: int = 100, max_chunks: int = 400) -> None:
+def write(name, w, out):
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), f"fstar_{name}.json")
+    with open(path, "w") as fh:
+        json.dump(out, fh, indent=1)
+    return path
+
+
+def main(name: str, chunk: int = 100, max_chunks: int = 400, cont_cg: int = 250) -> None:
     w = CONFIGS[name]()
     pr = oracle.Problem.from_workload(w)
     t0 = time.time()
@@ -60,7 +72,17 @@ def main(name: str, chunk: int = 100, max_chunks: int = 400) -> None:
             break
         f_prev = f
         prev = th.copy()
-        th, rep, _ = pr.fit(w.P, Theta0=th, eps_kkt=0.0, max_newton=chunk, start_stage=2)
+        # provisional record after every chunk (status "provisional" until a
+        # stopping rule holds)
+        write(name, w, {"config": w.name, "status": "provisional", "f_star": float(f),
+                        "f_lower": float(f - gap), "fw_gap": float(gap), "kkt": float(kkt),
+                        "iters_s1": totals["iters_s1"], "iters_s2": totals["iters_s2"],
+                        "seconds": time.time() - t0,
+                        "sample_rows": [int(r) for r in rows],
+                        "theta_rows": [[float(v) for v in th[r]] for r in rows]})
+        # continuation chunks: stage 2 (Algorithm 1) with longer CG solves
+        th, rep, _ = pr.fit(w.P, Theta0=th, eps_kkt=0.0, max_newton=chunk, start_stage=2,
+                            max_cg=cont_cg)
         for k in totals:
             totals[k] += rep[k]
         if rep["status"] == 3 and rep["iters_s2"] < 2:
@@ -70,8 +92,13 @@ def main(name: str, chunk: int = 100, max_chunks: int = 400) -> None:
             kkt = pr.kkt(th, G)
             print(f"{name}: stagnated at f={f:.16e} fw_gap={gap:.3e}", flush=True)
             break
+    th10, rep10, _ = pr.fit(w.P, eps_kkt=1e-10, max_newton=100000)
+    theta_tol = float(max(10.0 * np.abs(th10[rows] - th[rows]).max(), 1e-9))
+    print(f"{name}: eps 1e-10 run: f={rep10['f']:.16e} kkt={rep10['kkt']:.3e} "
+          f"theta_tol={theta_tol:.3e}", flush=True)
     out = {
         "config": w.name,
+        "status": "certified",
         "generator": f"workloads.config_{name}()",
         "oracle": "oracle.Problem.fit (FP64, Algorithm 3, then warm-started stage-2 chunks)",
         "f_star": float(f),
@@ -89,11 +116,10 @@ def main(name: str, chunk: int = 100, max_chunks: int = 400) -> None:
         "sample_rows": [int(r) for r in rows],
         "theta_rows": [[float(v) for v in th[r]] for r in rows],
         "theta_drift": drift,
+        "theta_tol": theta_tol,
+        "f_eps1e-10": float(rep10["f"]),
     }
-    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), f"fstar_{name}.json")
-    with open(path, "w") as fh:
-        json.dump(out, fh, indent=1)
-    print("wrote", path)
+    print("wrote", write(name, w, out))
 
 
 if __name__ == "__main__":

@@ -126,6 +126,28 @@ def test_apply_F_Ft_hvp(tomo, case, prec):
     assert np.all(np.abs(HV - HV_ref) <= tol * scale + 1e-300)
 
 
+# tensor-core Hessian products: bf16 hi/lo split operands (three products per
+# slice) with f32 accumulation keep ~16 significant bits per term; the f32
+# weights and accumulation add the FP32 errors above
+TOLTC = 2e-4
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_hvp_tensor_cores(tomo, case):
+    lam, rng, c = make(case)
+    M, N, D = c["M"], c["N"], len(lam)
+    pr = oracle.Problem(M, N, lam, c["band_k"], c["gamma"])
+    with tomo.Plan(M, N, lam, c["band_k"], c["gamma"], precision="tc") as pl:
+        for X in (rng.standard_normal((M, N)), workloads.random_feasible_theta(M, N, rng)):
+            HV = host(pl.hvp(dev(X)))
+            HV_ref = pr.hvp(X)
+            scale = 2 * pr.apply_Ft(pr.apply_F(np.abs(X))) + 8 * c["gamma"] * np.abs(X).max()
+            err = np.abs(HV - HV_ref) / (scale + 1e-300)
+            assert err.max() <= TOLTC, (case, err.max())
+            HV2 = host(pl.hvp(dev(X)))          # deterministic
+            np.testing.assert_array_equal(HV, HV2)
+
+
 def test_hess_diag(tomo):
     for case in CASES:
         lam, rng, c = make(case)
@@ -179,7 +201,7 @@ def load_gold(name):
         return json.load(fh)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "mixed", "tc"])
 def test_fit_c1_matches_certified_optimum(tomo, prec):
     w = workloads.config_c1()
     gold = load_gold("c1")
@@ -212,7 +234,7 @@ def test_fit_fp64_follows_oracle_iterates(tomo):
             np.testing.assert_allclose(Th_g, Th_o, atol=1e-8)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "mixed", "tc"])
 def test_fit_small_cases_reach_oracle_optimum(tomo, prec):
     for seed, kw in ((31, dict(M=96, bins=11, D=128, X=80.0, gamma=1e-3)),
                      (32, dict(M=77, bins=4, D=61, X=60.0, gamma=0.0, band_k=0.0)),
