@@ -19,7 +19,7 @@ if ROOT not in sys.path:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--config", default="c2", choices=["c1", "c2"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "mixed", "tc"])
     ap.add_argument("--newton", type=int, default=3)
     ap.add_argument("--op", default="fit", choices=["fit", "hvp", "fwd", "adj"],
                     help="fit: the solver; hvp/fwd/adj: --reps single products")
