@@ -208,6 +208,34 @@ tomo_status tomo_bands(tomo_plan_t plan, int64_t *lo_host, int64_t *hi_host);
  * all entry points), for launch accounting. */
 int64_t tomo_kernel_launches(void);
 
+/* ---- objective without a plan, allocating nothing -----------------------
+ * The paper has no counterpart of this entry point.  It is for callers that
+ * cannot allocate device memory where they need the objective: code that
+ * runs inside a memory pool or arena owning every allocation of the process,
+ * code inside a framework that forbids allocation (and its device
+ * synchronisation) in its hot loop, or callers whose memory is committed to
+ * their own buffers.  tomo_plan allocates tables and workspaces; this call
+ * allocates nothing and needs no plan.
+ *
+ * *f (one double, DEVICE memory) receives f = ||P - F Theta||^2 + gamma
+ * sum_n sum_{i<M-1} (Theta_{i,n} - Theta_{i+1,n})^2 in double, with the band
+ * of band_k as in tomo_desc.  lambda (D), P (D x N) and Theta (M x N) are
+ * DEVICE pointers; lambda need not be sorted.  Work is queued on `stream`
+ * (cudaStream_t, NULL: the legacy default stream); the call returns without
+ * waiting, f is ready when the stream reaches it.
+ *
+ * Its only scratch is a static device array of TOMO_NOALLOC_MAX_ROWS doubles
+ * (2 MiB) that every device loading the library holds until the library is
+ * unloaded; D + M above TOMO_NOALLOC_MAX_ROWS gives TOMO_EINVAL.  The first
+ * call on a device looks up that array's device address (make the first call
+ * before any stream capture).  All calls share the array: calls whose work
+ * overlaps on the GPU (different streams or threads) race and return wrong
+ * values; order them on one stream.  2 <= N <= 1024, M, D >= 1. */
+#define TOMO_NOALLOC_MAX_ROWS 262144
+tomo_status tomo_objective_noalloc(int64_t M, int64_t N, int64_t D, const double *lambda,
+                                   double band_k, double gamma, const double *P,
+                                   const double *Theta, double *f, void *stream);
+
 /* Message of the last failure on the calling thread ("" if none). */
 const char *tomo_last_error(void);
 

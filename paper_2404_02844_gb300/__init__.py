@@ -74,6 +74,8 @@ EXPORTS = [
     ("tomo_kkt", c_i32, [c_ptr, c_ptr, c_ptr, ctypes.POINTER(c_dbl)]),
     ("tomo_poisson_weights", c_i32, [c_ptr, c_ptr, c_ptr, c_i64, c_ptr]),
     ("tomo_bands", c_i32, [c_ptr, c_ptr, c_ptr]),
+    ("tomo_objective_noalloc", c_i32, [c_i64, c_i64, c_i64, c_ptr, c_dbl, c_dbl, c_ptr, c_ptr,
+                                       c_ptr, c_ptr]),
     ("tomo_kernel_launches", c_i64, []),
     ("tomo_last_error", ctypes.c_char_p, []),
 ]

@@ -38,6 +38,12 @@ static tomo_status fail(tomo_status s, const char *fmt, ...)
     return s;
 }
 
+tomo_status tomo_set_error(tomo_status s, const char *msg)
+{
+    g_err = msg;
+    return s;
+}
+
 #define CUDA_TRY(expr)                                                                     \
     do {                                                                                   \
         cudaError_t _e = (expr);                                                           \

@@ -156,6 +156,9 @@ inline bool hvp_on_tensor_cores(int precision) { return precision == TOMO_PREC_T
 cudaError_t launch_hvp_tc(Plan &p, const double *V, double *HV, bool gated);
 size_t tc_smem_bytes(int bn);
 
+// records a failure message for tomo_last_error (api.cu)
+tomo_status tomo_set_error(tomo_status s, const char *msg);
+
 // kernel launch accounting (all threads)
 void count_launch(int n = 1);
 
