@@ -320,7 +320,7 @@ def main():
             "data": "synthetic (seeded PCG64; stands in for the paper's experimental data)",
             "config": {"workload": WORKLOAD, "global_batch": world, "seq_len": M,
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                       "form": "chosen: tensor-core CG Hessian products (bf16 hi/lo x3), FP32 line-search products, FP64 gradient/residual/reductions",
+                       "form": "chosen: tensor-core CG Hessian products (bf16 hi/lo x3), FP32 line-search products and gradient, FP64 residual refresh/objective/reductions",
                        "l2": "flushed (512 MB write) before every timed solve"},
             "time_to_tolerance_s": ttt,
             "rel_gap": gap,

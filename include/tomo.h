@@ -59,9 +59,12 @@ typedef enum {
  *         + g(Theta + s) - g(Theta) reduced in double. */
 /*   MIXED: as FP32 for the CG Hessian products and the line-search products,
  *         but the gradient F^T R is contracted in double.
- *   TC:   as MIXED, but the CG Hessian products run on the tensor cores
- *         (tcgen05.mma, bf16 operands split into hi + lo parts, three products
- *         per slice, f32 accumulation in tensor memory: ~16 significant bits). */
+ *   TC:   the CG Hessian products run on the tensor cores (tcgen05.mma,
+ *         bf16 operands split into hi + lo parts, three products per slice,
+ *         f32 accumulation in tensor memory: ~16 significant bits); the
+ *         line-search products F s and the gradient F^T R are contracted in
+ *         float (the Armijo test needs float-grade F s); residual refreshes,
+ *         the objective and every reduction in double. */
 typedef enum {
     TOMO_PREC_FP64 = 0,
     TOMO_PREC_FP32 = 1,
@@ -166,6 +169,20 @@ void tomo_fit_opts_default(tomo_fit_opts *opts);
  * the iteration cap. */
 tomo_status tomo_fit(tomo_plan_t plan, const double *P, double *Theta,
                      const tomo_fit_opts *opts, tomo_fit_report *report);
+
+/* Batch of independent problems (for instance one data set at several gamma,
+ * or many detectors): each instance k gets its own plan (built from
+ * descs[k]) and is solved by tomo_fit(P[k], Theta[k], opts), up to
+ * `concurrency` instances at a time (<= 0: 8), each on its plan's own work
+ * stream so that small instances share the GPU.  Plans are built and freed
+ * inside the call, so memory is bounded by the concurrent instances.  Every
+ * plan fences descs[k].stream into its work stream on entry and back on exit.
+ * statuses[k] receives each instance's status, reports[k] (may be NULL) its
+ * report.  Returns TOMO_OK if every instance returned TOMO_OK or
+ * TOMO_ENOTCONV, else the first other failure. */
+tomo_status tomo_fit_batched(const tomo_desc *descs, const double *const *P, double *const *Theta,
+                             int32_t count, const tomo_fit_opts *opts, tomo_fit_report *reports,
+                             tomo_status *statuses, int32_t concurrency);
 
 /* ---- single steps of the hot path (device pointers only) ----------------
  * Exposed so that every step can be checked on its own; the solver calls the

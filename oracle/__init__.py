@@ -76,6 +76,7 @@ def lib():
         L.orc_bands.argtypes = [c_ptr, c_ptr, c_ptr]
         for name in ("orc_apply_F", "orc_apply_Ft", "orc_hvp"):
             getattr(L, name).argtypes = [c_ptr, c_ptr, c_ptr]
+        L.orc_dense_F.argtypes = [c_ptr, c_ptr]
         L.orc_apply_F_rows.argtypes = [c_ptr, c_ptr, c_ptr, c_i64, c_ptr]
         L.orc_apply_Ft_rows.argtypes = [c_ptr, c_ptr, c_ptr, c_i64, c_ptr]
         L.orc_regulariser.restype = c_dbl
@@ -168,6 +169,12 @@ class Problem:
         hi = np.empty(self.D, np.int64)
         lib().orc_bands(self._h, _p(lo), _p(hi))
         return lo, hi
+
+    def dense_F(self) -> np.ndarray:
+        """F as a dense D x M array (Eq. Fmatrix, zero outside the bands)."""
+        out = np.empty((self.D, self.M))
+        lib().orc_dense_F(self._h, _p(out))
+        return out
 
     # --- products ------------------------------------------------------
     def apply_F(self, X) -> np.ndarray:

@@ -158,6 +158,15 @@ static inline double Fval(const orc_problem *p, int64_t d, int64_t i)
     return orc_poisson(i, p->lam[d]);
 }
 
+/* Dense D x M copy of F (Eq. Fmatrix, zero outside the bands). */
+ORC_API void orc_dense_F(const orc_problem *p, double *out)
+{
+    const int64_t M = p->M;
+#pragma omp parallel for
+    for (int64_t d = 0; d < p->D; ++d)
+        for (int64_t i = 0; i < M; ++i) out[d * M + i] = Fval(p, d, i);
+}
+
 /* ---------------------------------------------------------------------- */
 /* Products with F (Table ops: objective / gradient / Hessian products)    */
 /* ---------------------------------------------------------------------- */

@@ -66,6 +66,9 @@ EXPORTS = [
     ("tomo_fit_opts_default", None, [ctypes.POINTER(tomo_fit_opts)]),
     ("tomo_fit", c_i32, [c_ptr, c_ptr, c_ptr, ctypes.POINTER(tomo_fit_opts),
                          ctypes.POINTER(tomo_fit_report)]),
+    ("tomo_fit_batched", c_i32, [ctypes.POINTER(tomo_desc), ctypes.POINTER(c_ptr),
+                                 ctypes.POINTER(c_ptr), c_i32, ctypes.POINTER(tomo_fit_opts),
+                                 ctypes.POINTER(tomo_fit_report), ctypes.POINTER(c_i32), c_i32]),
     ("tomo_apply_F", c_i32, [c_ptr, c_ptr, c_ptr]),
     ("tomo_apply_Ft", c_i32, [c_ptr, c_ptr, c_ptr]),
     ("tomo_hvp", c_i32, [c_ptr, c_ptr, c_ptr]),
@@ -140,6 +143,46 @@ def tomo_fit(h: int, P: int, Theta: int, opts: tomo_fit_opts | None = None):
                         ctypes.byref(rep))
     _check(st, "tomo_fit", allow=(0, 4))
     return st, rep
+
+
+def tomo_fit_batched(descs, P_ptrs, Theta_ptrs, opts=None, concurrency=8):
+    """Solves len(descs) independent problems; returns (statuses, reports)."""
+    n = len(descs)
+    D = (tomo_desc * n)(*descs)
+    Pp = (c_ptr * n)(*P_ptrs)
+    Tp = (c_ptr * n)(*Theta_ptrs)
+    reps = (tomo_fit_report * n)()
+    sts = (c_i32 * n)()
+    st = lib().tomo_fit_batched(D, Pp, Tp, n, ctypes.byref(opts) if opts is not None else None,
+                                reps, sts, concurrency)
+    _check(st, "tomo_fit_batched", allow=(0,))
+    return [int(x) for x in sts], [_fit_dict(r) for r in reps]
+
+
+def fit_batched(problems, precision="fp32", concurrency=8, **opts):
+    """problems: list of (M, N, lam, band_k, gamma, P, Theta) with P, Theta
+    float64 CUDA tensors (Theta receives the result).  Returns (statuses,
+    reports)."""
+    prec = {"fp64": PREC_FP64, "fp32": PREC_FP32, "mixed": PREC_MIXED, "tc": PREC_TC}[precision]
+    o = tomo_fit_opts_default()
+    for k, v in opts.items():
+        setattr(o, k, v)
+    keep, descs, Pp, Tp = [], [], [], []
+    stream = None
+    try:
+        import torch
+        if torch.cuda.is_available():
+            stream = torch.cuda.current_stream().cuda_stream
+    except ImportError:
+        pass
+    for (M, N, lam, band_k, gamma, P, Theta) in problems:
+        lam = np.ascontiguousarray(lam, dtype=np.float64)
+        keep.append(lam)
+        descs.append(tomo_desc(int(M), int(N), lam.shape[0], lam.ctypes.data, float(band_k),
+                               float(gamma), prec, 0, stream or None, 0))
+        Pp.append(_ptr(P))
+        Tp.append(_ptr(Theta))
+    return tomo_fit_batched(descs, Pp, Tp, o, concurrency)
 
 
 def tomo_apply_F(h, X, O):

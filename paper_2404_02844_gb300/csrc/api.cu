@@ -14,6 +14,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <thread>
 #include <utility>
 #include <vector>
 
@@ -97,6 +98,15 @@ static void free_plan(Plan *p)
     void *mir[] = {p->ut_hi, p->ut_lo, p->ot_hi, p->ot_lo};
     for (void *d : mir)
         if (d) cudaFree(d);
+    for (auto &row : p->cg_exec)
+        for (cudaGraphExec_t &g : row)
+            if (g) cudaGraphExecDestroy(g);
+    if (p->prof_ev_ready)
+        for (auto &row : p->prof_ev)
+            for (cudaEvent_t &e : row) cudaEventDestroy(e);
+    if (p->ev_in) cudaEventDestroy(p->ev_in);
+    if (p->ev_out) cudaEventDestroy(p->ev_out);
+    if (p->work) cudaStreamDestroy(p->work);
     if (p->sc_host) cudaFreeHost(p->sc_host);
     if (p->scratch_host) cudaFreeHost(p->scratch_host);
     if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
@@ -342,6 +352,9 @@ tomo_status tomo_plan(tomo_plan_t *out, const tomo_desc *d)
         PLAN_TRY(cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking));
         p->own_stream = true;
     }
+    PLAN_TRY(cudaStreamCreateWithFlags(&p->work, cudaStreamNonBlocking));
+    PLAN_TRY(cudaEventCreateWithFlags(&p->ev_in, cudaEventDisableTiming));
+    PLAN_TRY(cudaEventCreateWithFlags(&p->ev_out, cudaEventDisableTiming));
     const int64_t M = p->M, N = p->N, D = p->D, MN = M * N, DN = D * N;
     p->fwd_tiles = int((D + TILE_R - 1) / TILE_R);
     p->adj_tiles = int((M + TILE_R - 1) / TILE_R);
@@ -429,47 +442,81 @@ namespace tomo {
 // empty.  Stage 1 multiplies p itself, stage 2 the lifted u = E p.
 constexpr int CG_CHUNK = 4;
 
-// Events bracketing the band contractions of one CG chunk (profiling).
+// Events bracketing the band contractions of one CG chunk (profiling); they
+// live in the plan because captured graphs record them.
 struct ChunkEvents {
-    cudaEvent_t ev[CG_CHUNK][3];
-    bool ready = false;
-    tomo_status init()
-    {
-        if (ready) return TOMO_OK;
-        for (auto &row : ev)
-            for (auto &e : row) CUDA_TRY(cudaEventCreate(&e));
-        ready = true;
-        return TOMO_OK;
-    }
-    ~ChunkEvents()
-    {
-        if (!ready) return;
-        for (auto &row : ev)
-            for (auto &e : row) cudaEventDestroy(e);
-    }
+    cudaEvent_t (*ev)[3];
 };
 
-static tomo_status cg_chunk(Plan &p, int stage, int count, ChunkEvents *evs)
+static tomo_status prof_events(Plan &p, ChunkEvents *out)
+{
+    if (!p.prof_ev_ready) {
+        for (auto &row : p.prof_ev)
+            for (cudaEvent_t &e : row) CUDA_TRY(cudaEventCreate(&e));
+        p.prof_ev_ready = true;
+    }
+    out->ev = p.prof_ev;
+    return TOMO_OK;
+}
+
+static tomo_status cg_chunk(Plan &p, int stage, int count, const ChunkEvents *evs)
 {
     const double *in = stage == 1 ? p.p : p.u;
     const bool tc = hvp_on_tensor_cores(p.precision);
+    // while capturing, profiling events must become event-record nodes
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (evs) CUDA_TRY(cudaStreamIsCapturing(p.stream, &cap));
+    const unsigned evflag = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0u;
     for (int c = 0; c < count; ++c) {
-        if (evs) CUDA_TRY(cudaEventRecord(evs->ev[c][0], p.stream));
+        if (evs) CUDA_TRY(cudaEventRecordWithFlags(evs->ev[c][0], p.stream, evflag));
         if (tc) {
             // tensor cores: the whole Hessian product (forward + adjoint) is
             // timed as the "forward" interval, the adjoint interval is empty
             CUDA_TRY(launch_hvp_tc(p, in, p.q, true));
-            if (evs) CUDA_TRY(cudaEventRecord(evs->ev[c][1], p.stream));
+            if (evs) CUDA_TRY(cudaEventRecordWithFlags(evs->ev[c][1], p.stream, evflag));
         } else {
             CUDA_TRY(launch_forward(p, prec_products(p.precision), FWD_STORE, in, p.O, nullptr, true));
-            if (evs) CUDA_TRY(cudaEventRecord(evs->ev[c][1], p.stream));
+            if (evs) CUDA_TRY(cudaEventRecordWithFlags(evs->ev[c][1], p.stream, evflag));
             CUDA_TRY(launch_adjoint(p, prec_products(p.precision), ADJ_HESS, p.O, p.q, in, true));
         }
-        if (evs) CUDA_TRY(cudaEventRecord(evs->ev[c][2], p.stream));
+        if (evs) CUDA_TRY(cudaEventRecordWithFlags(evs->ev[c][2], p.stream, evflag));
         CUDA_TRY(launch_cg_restrict(p, stage));
         CUDA_TRY(launch_cg_update_xr(p, stage));
         CUDA_TRY(launch_cg_update_p(p, stage));
     }
+    return TOMO_OK;
+}
+
+// One chunk of CG iterations: launched directly the first time (which also
+// configures every kernel), then captured once into a CUDA graph per (stage,
+// profile) and replayed.
+static tomo_status run_cg_chunk(Plan &p, int stage, const ChunkEvents *evs)
+{
+    const int ks = stage - 1, kp = evs ? 1 : 0;
+    if (p.cg_exec[ks][kp]) {
+        CUDA_TRY(cudaGraphLaunch(p.cg_exec[ks][kp], p.stream));
+        count_launch(p.cg_exec_kernels[ks][kp]);
+        return TOMO_OK;
+    }
+    if (p.cg_direct_runs[ks][kp]++ < 1) return cg_chunk(p, stage, CG_CHUNK, evs);
+    const int64_t l0 = tomo_kernel_launches();
+    CUDA_TRY(cudaStreamBeginCapture(p.stream, cudaStreamCaptureModeThreadLocal));
+    tomo_status st = cg_chunk(p, stage, CG_CHUNK, evs);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(p.stream, &graph);
+    const int nk = int(tomo_kernel_launches() - l0);
+    count_launch(-nk);  // capture launched nothing
+    if (st != TOMO_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    CUDA_TRY(e);
+    e = cudaGraphInstantiate(&p.cg_exec[ks][kp], graph, 0);
+    cudaGraphDestroy(graph);
+    CUDA_TRY(e);
+    p.cg_exec_kernels[ks][kp] = nk;
+    CUDA_TRY(cudaGraphLaunch(p.cg_exec[ks][kp], p.stream));
+    count_launch(nk);
     return TOMO_OK;
 }
 
@@ -526,7 +573,7 @@ static tomo_status fit_impl(Plan &p, const double *P, const tomo_fit_opts &o, to
     const bool fp64 = p.precision == TOMO_PREC_FP64;
     const bool delta = !fp64;
     ChunkEvents evs;
-    if (o.profile) TOMO_TRY(evs.init());
+    if (o.profile) TOMO_TRY(prof_events(p, &evs));
     double f = 0.0;
     TOMO_TRY(residual_objective(p, P, p.Th, p.R, &f));
     rep.refreshes = 1;
@@ -556,7 +603,7 @@ static tomo_status fit_impl(Plan &p, const double *P, const tomo_fit_opts &o, to
         int active = p.sc_host->cg_active;
         int done = 0;
         while (active) {
-            TOMO_TRY(cg_chunk(p, stage, CG_CHUNK, o.profile ? &evs : nullptr));
+            TOMO_TRY(run_cg_chunk(p, stage, o.profile ? &evs : nullptr));
             TOMO_TRY(read_scalars(p));
             active = p.sc_host->cg_active;
             if (o.profile) {
@@ -638,6 +685,20 @@ tomo_status tomo_fit(tomo_plan_t plan, const double *P, double *Theta, const tom
     std::memset(&rep, 0, sizeof(rep));
     const int64_t l0 = tomo_kernel_launches();
     const auto t0 = std::chrono::steady_clock::now();
+    // the solve runs on the plan's work stream (capturable), fenced against
+    // the caller's stream on entry and exit
+    CUDA_TRY(cudaEventRecord(p.ev_in, p.stream));
+    CUDA_TRY(cudaStreamWaitEvent(p.work, p.ev_in, 0));
+    struct StreamSwap {
+        Plan &p;
+        cudaStream_t user;
+        explicit StreamSwap(Plan &pl) : p(pl), user(pl.stream) { p.stream = p.work; }
+        ~StreamSwap()
+        {
+            p.stream = user;
+            if (cudaEventRecord(p.ev_out, p.work) == cudaSuccess) cudaStreamWaitEvent(user, p.ev_out, 0);
+        }
+    } swap_guard(p);
     const int64_t MN = p.M * p.N, DN = p.D * p.N;
     const double *Pd;
     TOMO_TRY(stage_in(p, P, DN, &p.Pbuf, &Pd));
@@ -661,6 +722,45 @@ tomo_status tomo_fit(tomo_plan_t plan, const double *P, double *Theta, const tom
     rep.kernels = int32_t(tomo_kernel_launches() - l0);
     if (report) *report = rep;
     return rep.stop == 2 ? TOMO_ENOTCONV : TOMO_OK;
+}
+
+tomo_status tomo_fit_batched(const tomo_desc *descs, const double *const *P, double *const *Theta,
+                             int32_t count, const tomo_fit_opts *opts, tomo_fit_report *reports,
+                             tomo_status *statuses, int32_t concurrency)
+{
+    if (count < 0 || (count > 0 && (!descs || !P || !Theta || !statuses)))
+        return fail(TOMO_EINVAL, "invalid batch arguments");
+    if (count == 0) return TOMO_OK;
+    if (concurrency <= 0) concurrency = 8;
+    if (concurrency > count) concurrency = count;
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    std::atomic<int> next{0};
+    auto worker = [&]() {
+        cudaSetDevice(dev);
+        for (;;) {
+            const int k = next.fetch_add(1);
+            if (k >= count) break;
+            tomo_fit_report rep;
+            std::memset(&rep, 0, sizeof(rep));
+            tomo_plan_t pl = nullptr;
+            tomo_status st = tomo_plan(&pl, &descs[k]);
+            if (st == TOMO_OK) {
+                st = tomo_fit(pl, P[k], Theta[k], opts, &rep);
+                tomo_plan_destroy(pl);
+            }
+            statuses[k] = st;
+            if (reports) reports[k] = rep;
+        }
+    };
+    std::vector<std::thread> pool;
+    for (int t = 1; t < concurrency; ++t) pool.emplace_back(worker);
+    worker();
+    for (auto &th : pool) th.join();
+    for (int k = 0; k < count; ++k)
+        if (statuses[k] != TOMO_OK && statuses[k] != TOMO_ENOTCONV)
+            return fail(statuses[k], "instance %d failed", k);
+    return TOMO_OK;
 }
 
 tomo_status tomo_apply_F(tomo_plan_t plan, const double *X, double *O)

@@ -403,13 +403,10 @@ static cudaError_t launch_band_t(Plan &p, const BandArgs &a, int n_units, const 
 {
     auto kern = k_band<T, BN, FWD, MODE>;
     const size_t smem = sizeof(SmemTile<T, BN>);
-    static bool configured = false;  // one attribute call per instantiation
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             int(smem));
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    // one attribute call per instantiation (thread-safe static initialisation)
+    static const cudaError_t cfg =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (cfg != cudaSuccess) return cfg;
     dim3 grid(unsigned(n_units), unsigned((p.N + BN - 1) / BN));
     kern<<<grid, GEMM_THREADS, smem, p.stream>>>(a, In, out, aux);
     count_launch();

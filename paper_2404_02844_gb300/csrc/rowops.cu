@@ -340,7 +340,8 @@ __global__ void k_cg_restrict(RowArgs a, int stage, const int32_t *mrow, const u
     });
 }
 
-// x += alpha p, r -= alpha q, z = r / diag (free), with r.z and r.r.
+// x += alpha p, r -= alpha q, z = r / diag (free), with r.z and r.r; warp per
+// row (the diagonal is one value per row).
 __global__ void k_cg_update_xr(RowArgs a, int stage, const uint8_t *freem, const double *p,
                                const double *q, double *x, double *r, double *z)
 {
@@ -348,12 +349,12 @@ __global__ void k_cg_update_xr(RowArgs a, int stage, const uint8_t *freem, const
     const double al = a.sc->alpha;
     const double scale = stage == 1 ? 1.0 : 2.0;
     double rz = 0.0, rr = 0.0;
-    const int64_t MN = a.M * a.N;
-    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < MN;
-         e += int64_t(gridDim.x) * blockDim.x) {
+    ROW_LOOP_BEGIN
+    const double diag = scale * a.h[i];
+    for (int64_t n = lane; n < a.N; n += 32) {
+        const int64_t e = i * a.N + n;
         const double xv = x[e] + al * p[e];
         const double rv = r[e] - al * q[e];
-        const double diag = scale * a.h[e / a.N];
         const double zv = freem[e] ? rv / diag : 0.0;
         x[e] = xv;
         r[e] = rv;
@@ -361,6 +362,7 @@ __global__ void k_cg_update_xr(RowArgs a, int stage, const uint8_t *freem, const
         rz += rv * zv;
         rr += rv * rv;
     }
+    ROW_LOOP_END
     double v[2] = {rz, rr};
     DevScalars *sc = a.sc;
     grid_reduce<2>(v, a.partials, a.pstride, &sc->ticket[0], [sc](const double *t) {
@@ -414,16 +416,18 @@ __global__ void k_direction(RowArgs a, int stage, const uint8_t *var, const uint
 {
     const double scale = stage == 1 ? 1.0 : 2.0;
     double gd = 0.0;
-    const int64_t MN = a.M * a.N;
-    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < MN;
-         e += int64_t(gridDim.x) * blockDim.x) {
+    ROW_LOOP_BEGIN
+    const double diag = scale * a.h[i];
+    for (int64_t n = lane; n < a.N; n += 32) {
+        const int64_t e = i * a.N + n;
         double d;
         if (!var[e]) d = 0.0;
         else if (freem[e]) d = x[e];
-        else d = -g[e] / (scale * a.h[e / a.N]);
+        else d = -g[e] / diag;
         dir[e] = d;
         gd += g[e] * d;
     }
+    ROW_LOOP_END
     double v[1] = {gd};
     DevScalars *sc = a.sc;
     grid_reduce<1>(v, a.partials, a.pstride, &sc->ticket[0], [sc](const double *t) {
@@ -488,51 +492,73 @@ __device__ __forceinline__ void trial_row(const RowArgs &a, int stage, int64_t i
 
 // Trial point of the whole matrix with g^T (trial - Theta), the regulariser
 // (direct mode: g(trial); delta mode: g(trial) - g(Theta) from the exact
-// expansion) and the count of negative implicit entries.  Row i + 1 is
-// recomputed by the same warp for the nearest-neighbour term.
+// expansion) and the count of negative implicit entries.  A CTA owns blocks
+// of ROW_WARPS consecutive rows (one warp per row) and keeps their Theta and
+// trial rows, plus the next block's first row (recomputed by the last warp),
+// in shared memory for the nearest-neighbour term.
 template <int VPL>
 __global__ void k_trial(RowArgs a, int stage, double alpha, int delta, const double *Th,
                         const double *dir, const double *g, const int32_t *mrow,
                         const uint8_t *var, double *trial, double *s_out)
 {
+    extern __shared__ double trial_sm[];
+    double *sh_th = trial_sm;                              // [ROW_WARPS + 1][N]
+    double *sh_t = trial_sm + (ROW_WARPS + 1) * a.N;        // [ROW_WARPS + 1][N]
     const bool graddir = a.sc->use_grad_dir != 0;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     double gts = 0.0, reg = 0.0, negc = 0.0;
-    ROW_LOOP_BEGIN
-    double th[VPL], t[VPL];
-    bool neg;
-    trial_row<VPL>(a, stage, i, lane, alpha, graddir, Th, dir, g, mrow, var, th, t, neg);
-    if (lane == 0 && neg) negc += 1.0;
-    double sv[VPL];
+    const int64_t nblocks = (a.M + ROW_WARPS - 1) / ROW_WARPS;
+    for (int64_t b = blockIdx.x; b < nblocks; b += gridDim.x) {
+        const int64_t i0 = b * ROW_WARPS;
+        // own row, and the halo row (first row of the next block) by the last warp
+        for (int pass = 0; pass < (w == ROW_WARPS - 1 ? 2 : 1); ++pass) {
+            const int slot = pass == 0 ? w : ROW_WARPS;
+            const int64_t i = i0 + slot;
+            if (i >= a.M) continue;
+            double th[VPL], t[VPL];
+            bool neg;
+            trial_row<VPL>(a, stage, i, lane, alpha, graddir, Th, dir, g, mrow, var, th, t, neg);
 #pragma unroll
-    for (int k = 0; k < VPL; ++k) {
-        const int64_t n = lane + 32 * k;
-        sv[k] = t[k] - th[k];
-        if (n < a.N) {
-            const int64_t e = i * a.N + n;
-            trial[e] = t[k];
-            s_out[e] = sv[k];
-            if (var[e]) gts += g[e] * sv[k];
+            for (int k = 0; k < VPL; ++k) {
+                const int64_t n = lane + 32 * k;
+                if (n < a.N) {
+                    sh_th[slot * a.N + n] = th[k];
+                    sh_t[slot * a.N + n] = t[k];
+                }
+            }
+            if (pass == 0) {
+                if (lane == 0 && neg) negc += 1.0;
+#pragma unroll
+                for (int k = 0; k < VPL; ++k) {
+                    const int64_t n = lane + 32 * k;
+                    if (n < a.N) {
+                        const int64_t e = i * a.N + n;
+                        const double sv = t[k] - th[k];
+                        trial[e] = t[k];
+                        s_out[e] = sv;
+                        if (var[e]) gts += g[e] * sv;
+                    }
+                }
+            }
         }
-    }
-    if (a.gamma != 0.0 && i + 1 < a.M) {
-        double th1[VPL], t1[VPL];
-        bool neg1;
-        trial_row<VPL>(a, stage, i + 1, lane, alpha, graddir, Th, dir, g, mrow, var, th1, t1, neg1);
-#pragma unroll
-        for (int k = 0; k < VPL; ++k) {
-            if (lane + 32 * k < a.N) {
+        __syncthreads();
+        const int64_t i = i0 + w;
+        if (a.gamma != 0.0 && i + 1 < a.M) {
+            for (int64_t n = lane; n < a.N; n += 32) {
+                const double t0 = sh_t[w * a.N + n], t1 = sh_t[(w + 1) * a.N + n];
                 if (delta) {
-                    const double ds = sv[k] - (t1[k] - th1[k]);
-                    const double dth = th[k] - th1[k];
+                    const double th0 = sh_th[w * a.N + n], th1 = sh_th[(w + 1) * a.N + n];
+                    const double ds = (t0 - th0) - (t1 - th1);
+                    const double dth = th0 - th1;
                     reg += ds * ds + 2.0 * dth * ds;
                 } else {
-                    const double dt = t[k] - t1[k];
+                    const double dt = t0 - t1;
                     reg += dt * dt;
                 }
             }
         }
+        __syncthreads();
     }
-    ROW_LOOP_END
     double v[3] = {gts, a.gamma * reg, negc};
     DevScalars *sc = a.sc;
     grid_reduce<3>(v, a.partials, a.pstride, &sc->ticket[0], [sc, alpha](const double *t) {
@@ -692,8 +718,8 @@ cudaError_t launch_cg_restrict(Plan &p, int stage)
 cudaError_t launch_cg_update_xr(Plan &p, int stage)
 {
     RowArgs a = row_args(p);
-    k_cg_update_xr<<<elem_grid(p, p.M * p.N), 256, 0, p.stream>>>(a, stage, p.freem, p.p, p.q,
-                                                                  p.x, p.r, p.z);
+    k_cg_update_xr<<<row_grid(p), ROW_WARPS * 32, 0, p.stream>>>(a, stage, p.freem, p.p, p.q,
+                                                                 p.x, p.r, p.z);
     count_launch();
     return cudaGetLastError();
 }
@@ -708,8 +734,8 @@ cudaError_t launch_cg_update_p(Plan &p, int stage)
 cudaError_t launch_direction(Plan &p, int stage)
 {
     RowArgs a = row_args(p);
-    k_direction<<<elem_grid(p, p.M * p.N), 256, 0, p.stream>>>(a, stage, p.var, p.freem, p.x,
-                                                               p.g, p.dir);
+    k_direction<<<row_grid(p), ROW_WARPS * 32, 0, p.stream>>>(a, stage, p.var, p.freem, p.x,
+                                                              p.g, p.dir);
     count_launch();
     return cudaGetLastError();
 }
@@ -717,8 +743,26 @@ cudaError_t launch_direction(Plan &p, int stage)
 cudaError_t launch_trial(Plan &p, int stage, double alpha, bool delta_mode)
 {
     RowArgs a = row_args(p);
-    VPL_DISPATCH(p.N, k_trial, row_grid(p), a, stage, alpha, delta_mode ? 1 : 0, p.Th, p.dir,
-                 p.g, p.mrow, p.var, p.trial, p.s);
+    const size_t smem = sizeof(double) * 2 * (ROW_WARPS + 1) * size_t(p.N);
+    const unsigned grid = row_grid(p);
+    const int d = delta_mode ? 1 : 0;
+#define TRIAL_LAUNCH(V)                                                                            \
+    do {                                                                                           \
+        static const cudaError_t cfg_ = cudaFuncSetAttribute(                                      \
+            k_trial<V>, cudaFuncAttributeMaxDynamicSharedMemorySize,                               \
+            int(2 * (ROW_WARPS + 1) * MAX_N * sizeof(double)));                                    \
+        if (cfg_ != cudaSuccess) return cfg_;                                                      \
+        k_trial<V><<<grid, ROW_WARPS * 32, smem, p.stream>>>(a, stage, alpha, d, p.Th, p.dir, p.g, \
+                                                             p.mrow, p.var, p.trial, p.s);         \
+    } while (0)
+    if (p.N <= 32) TRIAL_LAUNCH(1);
+    else if (p.N <= 64) TRIAL_LAUNCH(2);
+    else if (p.N <= 128) TRIAL_LAUNCH(4);
+    else if (p.N <= 256) TRIAL_LAUNCH(8);
+    else if (p.N <= 512) TRIAL_LAUNCH(16);
+    else TRIAL_LAUNCH(32);
+#undef TRIAL_LAUNCH
+    count_launch();
     return cudaGetLastError();
 }
 

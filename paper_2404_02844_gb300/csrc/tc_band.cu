@@ -371,12 +371,9 @@ static cudaError_t launch_tc_t(Plan &p, const TcArgs &a)
 {
     auto kern = k_band_tc<BN, SPLIT, FWD>;
     const int smem = TcLayout<BN, SPLIT>::TOTAL;
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    static const cudaError_t cfg =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (cfg != cudaSuccess) return cfg;
     const Schedule &S = p.sched_tc[FWD ? 0 : 1];
     dim3 grid(unsigned(S.n_units), unsigned((p.N + BN - 1) / BN));
     kern<<<grid, TC_THREADS, smem, p.stream>>>(a);

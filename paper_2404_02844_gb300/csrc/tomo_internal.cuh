@@ -90,6 +90,16 @@ struct Plan {
     __nv_bfloat16 *ut_hi, *ut_lo, *ot_hi, *ot_lo;
     int64_t ut_pitch, ot_pitch;
 
+    // solver execution: a plan-owned non-blocking work stream fenced against
+    // the caller's stream, and CUDA graphs of the CG chunk per (stage, profile)
+    cudaStream_t work;
+    cudaEvent_t ev_in, ev_out;
+    cudaGraphExec_t cg_exec[2][2];
+    int cg_exec_kernels[2][2];
+    int cg_direct_runs[2][2];
+    cudaEvent_t prof_ev[4][3];
+    bool prof_ev_ready;
+
     // workspaces (device), M x N unless noted
     double *Th, *trial, *s, *G, *g, *x, *r, *z, *p, *u, *q, *dir;
     double *R, *Rt, *O;      // D x N
@@ -149,7 +159,10 @@ template <typename T> size_t band_smem_bytes(int bn);
 // arithmetic of the CG Hessian products / line-search products, and of the
 // gradient, for a plan precision
 inline int prec_products(int precision) { return precision == TOMO_PREC_FP64 ? TOMO_PREC_FP64 : TOMO_PREC_FP32; }
-inline int prec_gradient(int precision) { return precision == TOMO_PREC_FP32 ? TOMO_PREC_FP32 : TOMO_PREC_FP64; }
+inline int prec_gradient(int precision)
+{
+    return (precision == TOMO_PREC_FP32 || precision == TOMO_PREC_TC) ? TOMO_PREC_FP32 : TOMO_PREC_FP64;
+}
 inline bool hvp_on_tensor_cores(int precision) { return precision == TOMO_PREC_TC; }
 
 // tc_band.cu

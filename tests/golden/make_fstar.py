@@ -1,7 +1,8 @@
 """Writes the certified optimum of a synthetic configuration, computed by the
 FP64 oracle only (no GPU code is imported):
 
-    python tests/golden/make_fstar.py c1|c2
+    python tests/golden/make_fstar.py c1|c2            (iterative certification)
+    python tests/golden/make_fstar.py c2 --exact       (exact KKT solve, below)
 
 The oracle's solver (Algorithm 3) runs in chunks of Newton iterations, each
 chunk warm-started from the previous iterate (the first chunk is the plain
@@ -122,5 +123,53 @@ def main(name: str, chunk: int = 100, max_chunks: int = 400, cont_cg: int = 250)
     print("wrote", write(name, w, out))
 
 
+def main_exact(name: str, seed_iters: int = 100) -> None:
+    """Certification by the exact KKT solve (oracle.exact_qp): the oracle's
+    solver runs `seed_iters` Newton iterations (Algorithm 3) to provide a
+    support, then the active-set KKT solve finishes exactly; f* is certified
+    by the primal and dual violations of the final support."""
+    from oracle import exact_qp
+    w = CONFIGS[name]()
+    pr = oracle.Problem.from_workload(w)
+    t0 = time.time()
+    th_it, rep, hist = pr.fit(w.P, eps_kkt=0.0, max_newton=seed_iters)
+    print(f"{name}: seed solve f={rep['f']:.16e} kkt={rep['kkt']:.3e} t={time.time() - t0:.0f}s", flush=True)
+    th, nu, info = exact_qp.exact_optimum(pr.dense_F(), w.P, w.gamma, th_it,
+                                          log=lambda m: print(name, m, f"t={time.time() - t0:.0f}s", flush=True))
+    f, G = pr.gradient(w.P, th)
+    kkt = pr.kkt(th, G)
+    gap = pr.fw_gap(th, G)
+    print(f"{name}: exact f*={f:.16e} kkt={kkt:.3e} fw_gap={gap:.3e} {info}", flush=True)
+    rng = np.random.default_rng(workloads.BASE_SEED)
+    rows = np.unique(np.concatenate([[0, 1, w.M // 2, w.M - 1],
+                                     rng.choice(w.M, size=min(w.M, 60), replace=False)]))
+    out = {
+        "config": w.name,
+        "status": "certified",
+        "generator": f"workloads.config_{name}()",
+        "oracle": "oracle.exact_qp.exact_optimum (active-set KKT solve) seeded by oracle.Problem.fit",
+        "f_star": float(f),
+        "f_lower": float(f - gap),
+        "fw_gap": float(gap),
+        "kkt": float(kkt),
+        "kkt_primal_violation": info["primal_violation"],
+        "kkt_dual_violation_rel": info["dual_violation"],
+        "active_set_iterations": info["iterations"],
+        "support": info["support"],
+        "seed_iters": seed_iters,
+        "seed_f": float(rep["f"]),
+        "seconds": time.time() - t0,
+        "threads": oracle.num_threads(),
+        "rowsum_maxerr": float(np.abs(th.sum(1) - 1).max()),
+        "f_history_head": [float(x) for x in hist[:40]],
+        "sample_rows": [int(r) for r in rows],
+        "theta_rows": [[float(v) for v in th[r]] for r in rows],
+    }
+    print("wrote", write(name, w, out))
+
+
 if __name__ == "__main__":
-    main(sys.argv[1])
+    if len(sys.argv) > 2 and sys.argv[2] == "--exact":
+        main_exact(sys.argv[1])
+    else:
+        main(sys.argv[1])

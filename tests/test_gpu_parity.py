@@ -248,6 +248,20 @@ def test_fit_small_cases_reach_oracle_optimum(tomo, prec):
         assert (f - rep_o["f"]) / rep_o["f"] <= 1e-8, (seed, f, rep_o["f"], rep)
 
 
+@pytest.mark.parametrize("prec", ["fp32", "tc"])
+def test_fit_profile_events(tomo, prec):
+    """opts.profile times every CG band contraction (also when the CG chunk
+    is replayed from a CUDA graph) without changing the iterates."""
+    w = workloads.config_c1()
+    with tomo.Plan.from_workload(w, precision=prec) as pl:
+        Th0, rep0 = pl.fit(dev(w.P), eps_kkt=1e-12)
+        Th1, rep1 = pl.fit(dev(w.P), eps_kkt=1e-12, profile=1)
+    assert rep1["fwd_count"] == rep1["cg_total"] > 0
+    assert rep1["fwd_ms"] > 0.0
+    assert rep1["cg_total"] == rep0["cg_total"]
+    np.testing.assert_array_equal(host(Th0), host(Th1))
+
+
 def test_fit_host_buffers_and_warm_start(tomo):
     w = workloads.config_c1()
     with tomo.Plan.from_workload(w) as pl:
@@ -312,6 +326,37 @@ def test_c3_scale_products_on_sampled_rows(tomo):
             assert np.all(np.abs(Z_rows - refz) <= tol * scalez + 1e-300)
         del Xd
         Xd = dev(X)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "tc"])
+def test_fit_batched_matches_single_and_oracle(tomo, prec):
+    """Instances of the batched distribution (small M), each at the four
+    gamma values, solved in one batched call: every instance equals its
+    single-plan solve bit for bit (deterministic kernels, own work stream),
+    and the well-conditioned ones (gamma >= 1e-2) reach the oracle's optimum."""
+    insts = workloads.config_c4(n_instances=2, max_M=300)
+    opts = dict(eps_kkt=1e-10, max_newton=600)
+    problems, thetas, meta = [], [], []
+    for w in insts:
+        P = dev(w.P)
+        for g in workloads.C4_GAMMAS:
+            Th = torch.empty(w.M, w.N, dtype=torch.float64, device="cuda")
+            problems.append((w.M, w.N, w.lam, w.band_k, g, P, Th))
+            thetas.append(Th)
+            meta.append((w, g))
+    sts, reps = tomo.fit_batched(problems, precision=prec, concurrency=4, **opts)
+    assert all(s in (0, 4) for s in sts), sts
+    for (w, g), Th, rep in zip(meta, thetas, reps):
+        with tomo.Plan(w.M, w.N, w.lam, w.band_k, g, precision=prec) as pl:
+            Th1, rep1 = pl.fit(dev(w.P), **opts)
+        np.testing.assert_array_equal(host(Th), host(Th1))
+        assert rep["cg_total"] == rep1["cg_total"]
+        assert np.abs(host(Th).sum(1) - 1).max() < 1e-12 and host(Th).min() >= 0.0
+        if g >= 1e-2:
+            pr = oracle.Problem(w.M, w.N, w.lam, w.band_k, g)
+            _, rep_o, _ = pr.fit(w.P, **opts)
+            f = pr.objective(w.P, host(Th))
+            assert (f - rep_o["f"]) / rep_o["f"] <= 1e-8, (g, f, rep_o["f"], rep)
 
 
 def test_degenerate_problems(tomo):

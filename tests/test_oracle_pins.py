@@ -450,3 +450,29 @@ def test_detector_model_occupancy_closed_form():
                 occ = Fraction(math.comb(B, c) * math.factorial(c)) * stirling2(k, c) / Fraction(B) ** k
                 p += pk * occ
             assert theta[i, c] == pytest.approx(float(p), abs=1e-14)
+
+
+def test_exact_kkt_solve_matches_brute_force_and_iterative_solver():
+    """oracle.exact_qp: the active-set solution of the KKT conditions equals
+    the brute-force optimum (tiny) from a poor seed, and the iterative
+    oracle's optimum on c1."""
+    from oracle import exact_qp
+    rng = np.random.default_rng(21)
+    for seed in range(3):
+        M, N, D = 4, 3, 9
+        lam = np.sort(rng.uniform(0.0, 6.0, D))
+        P = rng.dirichlet(np.ones(N), D)
+        F = dense_F(M, lam, 0.0)
+        T_ref = brute_force_qp(F, P, 0.05)
+        seed_th = np.full((M, N), 1.0 / N)      # full support: corrections needed
+        Th, nu, info = exact_qp.exact_optimum(F, P, 0.05, seed_th)
+        np.testing.assert_allclose(Th, T_ref, atol=1e-9)
+    w = workloads.config_c1()
+    pr = oracle.Problem.from_workload(w)
+    Th_it, rep, _ = pr.fit(w.P, eps_kkt=1e-12)
+    Th, nu, info = exact_qp.exact_optimum(pr.dense_F(), w.P, w.gamma, Th_it)
+    f_exact = pr.objective(w.P, Th)
+    assert info["primal_violation"] <= 1e-13 and info["dual_violation"] <= 1e-13
+    assert f_exact <= rep["f"] * (1 + 1e-13)
+    assert f_exact == pytest.approx(rep["f"], rel=1e-11)
+    np.testing.assert_allclose(Th.sum(1), 1.0, atol=1e-12)

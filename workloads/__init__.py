@@ -208,6 +208,27 @@ def config_c2(shots=10_000_000) -> Workload:
                          1e-2, 10.0, shots, BASE_SEED + 1, p_dark=1e-4)
 
 
+C4_GAMMAS = (1e-4, 1e-3, 1e-2, 1e-1)
+
+
+def config_c4(n_instances=256, max_M=8192, shots=1_000_000):
+    """Batched instances: M ~ U{256..max_M}, N ~ U{8..128} (bins = N - 1),
+    efficiency U[0.3, 0.95], D = 2M probes with lambda linear in [0, 0.75 M],
+    1e6 shots; each to be solved at gamma in C4_GAMMAS.  Instance j uses seed
+    BASE_SEED + 3 + 1000 j."""
+    out = []
+    for j in range(n_instances):
+        seed = BASE_SEED + 3 + 1000 * j
+        rng = np.random.Generator(np.random.PCG64(seed))
+        M = int(rng.integers(256, max_M + 1))
+        N = int(rng.integers(8, 129))
+        eta = float(rng.uniform(0.3, 0.95))
+        D = 2 * M
+        out.append(make_workload(f"c4_{j}_M{M}_N{N}", M, N - 1, eta, D, 0.75 * M, C4_GAMMAS[0],
+                                 10.0, shots, seed))
+    return out
+
+
 def small_case(M=48, bins=7, eta=0.75, D=80, X=40.0, gamma=1e-3, band_k=10.0,
                shots=100_000, seed=BASE_SEED + 77, p_dark=0.0, crosstalk=0.0):
     """A scaled-down instance of the same construction (tests)."""
