@@ -33,7 +33,8 @@
  *   I set:  eps_k = min(eps_bar, w_k), w_k = || x - P(x - grad) ||_2 with P the
  *           stage's projection (simplex rows in stage 1, max(0,.) in stage 2).
  *   CG:     p0 = 0; stop when ||r|| <= min(0.5, sqrt(||b||)) ||b|| or after
- *           max_cg Hessian products; non-descent result -> p = -grad / diag.
+ *           max_cg (default 500) Hessian products; non-descent result ->
+ *           p = -grad / diag.
  *   Armijo: accept the smallest m with f(x(beta^m)) <= f(x) + c grad^T
  *           (x(beta^m) - x) (projected-arc form), beta = 3/4, c = 1/10.
  *   switch: |grad^T (x_{k+1} - x_k) / alpha_k| <= 1e-4, or two failed stage-1
@@ -514,7 +515,7 @@ ORC_API void orc_default_opts(orc_opts *o)
     o->f_target = 0.0;
     o->max_newton = 1000;
     o->max_stage1 = 200;
-    o->max_cg = 50;
+    o->max_cg = 500;
     o->ls_max = 50;
     o->start_stage = 1;
     o->warm_start = 0;

@@ -156,7 +156,7 @@ static tomo_status check_finite(Plan &p, const double *x, int64_t n, const char 
 //          to the tile's start
 static cudaError_t make_schedule(Plan &p, Schedule &S, const std::vector<int64_t> &st,
                                  const std::vector<int64_t> &en, int align, size_t part_elem_bytes,
-                                 int64_t *max_ctas)
+                                 int64_t *max_ctas, int64_t max_kc = INT64_MAX)
 {
     const int tiles = int(st.size());
     const int bn = band_bn(p.N);
@@ -166,6 +166,7 @@ static cudaError_t make_schedule(Plan &p, Schedule &S, const std::vector<int64_t
     const int64_t target = std::max<int64_t>(1, 4 * int64_t(p.num_sms) / ncol);
     int64_t kc = std::max<int64_t>(4 * int64_t(align), (W + target - 1) / target);
     kc = ((kc + align - 1) / align) * align;
+    if (kc > max_kc) kc = max_kc;
     std::vector<WorkUnit> units;
     std::vector<int32_t> first(tiles, 0), nsplit(tiles, 1);
     int64_t slots = 0;
@@ -244,7 +245,8 @@ static cudaError_t build_schedules(Plan &p, bool tensor_cores)
         for (int dir = 0; dir < 2; ++dir) {
             std::vector<int64_t> st, en;
             ranges(dir == 0, 64, 64, st, en);
-            if ((e = make_schedule(p, p.sched_tc[dir], st, en, 64, sizeof(float), &max_ctas)))
+            if ((e = make_schedule(p, p.sched_tc[dir], st, en, 64, sizeof(float), &max_ctas,
+                                   TC_MAX_UNIT)))
                 return e;
         }
         const int64_t npad = ((p.N + 127) / 128) * 128;
@@ -295,7 +297,7 @@ void tomo_fit_opts_default(tomo_fit_opts *o)
     o->f_target = 0.0;
     o->max_newton = 1000;
     o->max_stage1 = 200;
-    o->max_cg = 50;
+    o->max_cg = 500;
     o->ls_max = 50;
     o->start_stage = 1;
     o->warm_start = 0;

@@ -44,7 +44,11 @@ struct TcLayout {
     static constexpr int STAGE_BYTES = NPART * (A_BYTES + B_BYTES);
     static constexpr int STAGING_BYTES = (TC_THREADS / 8) * 8 * 9 * 4;  // 8x8 transposes (+pad)
     static constexpr int CTRL_BYTES = 64;
-    static constexpr int TOTAL = 1024 + TC_STAGES * STAGE_BYTES + STAGING_BYTES + CTRL_BYTES;
+    // per-unit tables: probe metadata (adjoint) and the 1/(i+1) pairs
+    static constexpr int META_BYTES = TC_MAX_UNIT * 24;
+    static constexpr int RINV_BYTES = (TC_MAX_UNIT + 2 * RUN + TILE_R) * 8;
+    static constexpr int TOTAL = 1024 + TC_STAGES * STAGE_BYTES + STAGING_BYTES + CTRL_BYTES +
+                                 META_BYTES + RINV_BYTES;
     static constexpr int TMEM_COLS = BN < 32 ? 32 : BN;
 };
 
@@ -95,6 +99,58 @@ __device__ __forceinline__ void tc_gen_run(const TcArgs &a, int64_t d, int64_t i
     }
 }
 
+struct ProbeMeta {
+    int32_t lo, hi;     // band (lo > hi: empty)
+    int64_t aoff;       // first anchor of the probe
+    float2 lam;         // lambda as float hi + lo
+};
+
+__device__ __forceinline__ ProbeMeta load_meta(const TcArgs &a, int64_t d)
+{
+    ProbeMeta m;
+    if (d < a.D) {
+        m.lo = a.lo[d];
+        m.hi = a.hi[d];
+        m.aoff = a.aoff[d];
+        m.lam = a.lam2[d];
+    } else {
+        m.lo = 1;
+        m.hi = 0;
+        m.aoff = 0;
+        m.lam = make_float2(0.f, 0.f);
+    }
+    return m;
+}
+
+// Same run as tc_gen_run, from the probe's metadata and a shared-memory slice
+// of the 1/(i+1) pairs (rs[i - rbase] = 1/(i+1)).
+__device__ __forceinline__ void tc_gen_run_tbl(const float *anchor, const ProbeMeta &m, int64_t i_r,
+                                               const float2 *rs, int64_t rbase, float (&v8)[RUN])
+{
+#pragma unroll
+    for (int t = 0; t < RUN; ++t) v8[t] = 0.f;
+    if (i_r + RUN - 1 < m.lo || i_r > m.hi) return;
+    const int64_t a0 = int64_t(m.lo) & ~int64_t(RUN - 1);
+    float v = anchor[m.aoff + (i_r - a0) / RUN];
+#pragma unroll
+    for (int t = 0; t < RUN; ++t) {
+        const int64_t i = i_r + t;
+        v8[t] = (i >= m.lo && i <= m.hi) ? v : 0.f;
+        const float2 r = rs[i - rbase];
+        v = v * fmaf(m.lam.x, r.x, fmaf(m.lam.x, r.y, m.lam.y * r.x));
+    }
+}
+
+// 16-byte asynchronous global -> shared copy
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(tc::smem_u32(smem_dst)), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
 // Packs 8 floats into hi and lo bf16 chunks (hi = rn(v), lo = rn(v - hi)).
 __device__ __forceinline__ void split_pack(const float (&v)[8], uint4 &hi, uint4 &lo)
 {
@@ -124,12 +180,29 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(TcArgs a)
     float *staging = reinterpret_cast<float *>(sm + TC_STAGES * L::STAGE_BYTES);
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + TC_STAGES * L::STAGE_BYTES + L::STAGING_BYTES);
     uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + TC_STAGES);
+    ProbeMeta *meta_s = reinterpret_cast<ProbeMeta *>(sm + TC_STAGES * L::STAGE_BYTES + L::STAGING_BYTES +
+                                                      L::CTRL_BYTES);
+    float2 *rinv_s = reinterpret_cast<float2 *>(reinterpret_cast<unsigned char *>(meta_s) + L::META_BYTES);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const WorkUnit wu = a.units[blockIdx.x];
     const int tile = wu.tile;
     const int64_t r0 = int64_t(tile) * TILE_R;
     const int64_t n0 = int64_t(blockIdx.y) * BN;
+
+    // unit tables: the 1/(i+1) pairs of every photon number the unit touches
+    // (forward: the unit's photon range; adjoint: the tile's photon range)
+    // and, for the adjoint, the metadata of the unit's probes
+    const int64_t rbase = FWD ? int64_t(wu.k0) : r0;
+    const int64_t rcount = FWD ? int64_t(wu.k1 - wu.k0) + 2 * RUN : int64_t(TILE_R) + 2 * RUN;
+    for (int64_t k = tid; k < rcount; k += TC_THREADS) {
+        const int64_t idx = rbase + k + 1;
+        rinv_s[k] = idx < a.M + RUN + 1 ? a.rinv2[idx] : make_float2(0.f, 0.f);
+    }
+    if (!FWD)
+        for (int64_t k = tid; k < int64_t(wu.k1 - wu.k0); k += TC_THREADS) meta_s[k] = load_meta(a, wu.k0 + k);
+    // forward: every thread generates the runs of one probe (row tid % 128)
+    const ProbeMeta my_meta = FWD ? load_meta(a, r0 + (tid % TILE_R)) : ProbeMeta{1, 0, 0, make_float2(0.f, 0.f)};
 
     if (warp == 0) {
         tc::tmem_alloc(tmem_holder, L::TMEM_COLS);
@@ -162,6 +235,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(TcArgs a)
         }
         const int64_t k0 = int64_t(wu.k0) + int64_t(s) * TC_BK;
 
+        // ---- operand B: transposed bf16 copy of the vector (asynchronous) ----
+        constexpr int BCH = BN * (TC_BK / 8);          // 16-byte chunks per part
+#pragma unroll
+        for (int q = 0; q < (L::NPART * BCH + TC_THREADS - 1) / TC_THREADS; ++q) {
+            const int c = tid + q * TC_THREADS;
+            if (c < L::NPART * BCH) {
+                const int part = c / BCH, cc = c % BCH;
+                const int n = cc / (TC_BK / 8), j = cc % (TC_BK / 8);
+                const __nv_bfloat16 *src = (part == 0 ? a.b_hi : a.b_lo) + (n0 + n) * a.bpitch + k0 + j * 8;
+                cp_async16((part == 0 ? B_hi : B_lo) + tc::sw128_chunk(n, j), src);
+            }
+        }
         // ---- operand A: Poisson weights ----
 #pragma unroll
         for (int q = 0; q < (TILE_R * TC_BK / RUN) / TC_THREADS; ++q) {
@@ -172,7 +257,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(TcArgs a)
                 // row = probe r0 + r, chunk = photon numbers k0 + 8 j .. + 7
                 row = run % TILE_R;
                 chunk = run / TILE_R;
-                tc_gen_run(a, r0 + row, k0 + int64_t(chunk) * RUN, v8);
+                tc_gen_run_tbl(a.anchor, my_meta, k0 + int64_t(chunk) * RUN, rinv_s, rbase, v8);
             } else {
                 // 8 x 8 block (8 probes x 8 photon numbers) per group of 8
                 // lanes, transposed through shared memory so that one lane
@@ -180,7 +265,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(TcArgs a)
                 const int g = run >> 3, t = run & 7;
                 const int pb = g % (TILE_R / 8), kb = g / (TILE_R / 8);
                 float w8[RUN];
-                tc_gen_run(a, k0 + kb * 8 + t, r0 + pb * 8, w8);
+                const int64_t pk = k0 + kb * 8 + t - wu.k0;   // probe index within the unit
+                const ProbeMeta m = (k0 + kb * 8 + t < wu.k1) ? meta_s[pk] : ProbeMeta{1, 0, 0, make_float2(0.f, 0.f)};
+                tc_gen_run_tbl(a.anchor, m, r0 + pb * 8, rinv_s, rbase, w8);
                 float *stg = staging + ((tid >> 3) * 8) * 9;
 #pragma unroll
                 for (int j = 0; j < RUN; ++j) stg[t * 9 + j] = w8[j];
@@ -196,19 +283,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(TcArgs a)
             *reinterpret_cast<uint4 *>(A_hi + tc::sw128_chunk(row, chunk)) = hi;
             if (SPLIT == 3) *reinterpret_cast<uint4 *>(A_lo + tc::sw128_chunk(row, chunk)) = lo;
         }
-        // ---- operand B: transposed bf16 copy of the vector ----
-        constexpr int BCH = BN * (TC_BK / 8);          // 16-byte chunks per part
-#pragma unroll
-        for (int q = 0; q < (L::NPART * BCH + TC_THREADS - 1) / TC_THREADS; ++q) {
-            const int c = tid + q * TC_THREADS;
-            if (c < L::NPART * BCH) {
-                const int part = c / BCH, cc = c % BCH;
-                const int n = cc / (TC_BK / 8), j = cc % (TC_BK / 8);
-                const __nv_bfloat16 *src = (part == 0 ? a.b_hi : a.b_lo) + (n0 + n) * a.bpitch + k0 + j * 8;
-                const uint4 val = *reinterpret_cast<const uint4 *>(src);
-                *reinterpret_cast<uint4 *>((part == 0 ? B_hi : B_lo) + tc::sw128_chunk(n, j)) = val;
-            }
-        }
+        cp_async_wait_all();
         tc::fence_proxy_async_smem();
         tc::tc_fence_before_sync();
         __syncthreads();

@@ -23,6 +23,7 @@ namespace tomo {
 constexpr int RUN = 8;
 constexpr int TILE_R = 128;
 constexpr int GEMM_THREADS = 256;
+constexpr int TC_MAX_UNIT = 1024;         // longest reduction range of a tensor-core work unit
 constexpr int ROW_WARPS = 8;              // warps per CTA in row kernels
 constexpr int MAX_N = 1024;               // outcomes supported by row kernels
 constexpr int RED_SLOTS = 4;              // partial-sum slots per reduction

@@ -25,8 +25,8 @@ MUTANTS = {
                                   "for (int64_t k = 0; k < MN; ++k) G[k] *= 1.0;"),
     "residual_sign": ("        O[k] -= P[k];", "        O[k] = P[k] + O[k];"),
     "poisson_off_by_one": ("lgammal((long double)i + 1.0L)", "lgammal((long double)i)"),
-    "adjoint_transposed_index": ("            double f = Fval(p, d, i);\n            const double *y = Y + d * N;",
-                                 "            double f = Fval(p, d, i < p->M - 1 ? i + 1 : i);\n            const double *y = Y + d * N;"),
+    "adjoint_transposed_index": ("            const double f = Fval(p, d, i);\n            const double *restrict y = Y + d * N;",
+                                 "            const double f = Fval(p, d, i < p->M - 1 ? i + 1 : i);\n            const double *restrict y = Y + d * N;"),
     "projection_threshold": ("        double t = (cum - 1.0) / (double)(k + 1);", "        double t = (cum - 1.0) / (double)(k + 2);"),
     "stage2_reduced_gradient_sign": ("                    w->g[k] = w->G[k] - gm;", "                    w->g[k] = gm - w->G[k];"),
     "armijo_sign": ("        if (ft <= f + o->c * gts) {", "        if (ft <= f - o->c * gts) {"),
