@@ -156,14 +156,15 @@ static tomo_status check_finite(Plan &p, const double *x, int64_t n, const char 
 //          to the tile's start
 static cudaError_t make_schedule(Plan &p, Schedule &S, const std::vector<int64_t> &st,
                                  const std::vector<int64_t> &en, int align, size_t part_elem_bytes,
-                                 int64_t *max_ctas, int64_t max_kc = INT64_MAX)
+                                 int64_t *max_ctas, int64_t max_kc = INT64_MAX,
+                                 int64_t units_per_sm = 4)
 {
     const int tiles = int(st.size());
     const int bn = band_bn(p.N);
     const int64_t ncol = (p.N + bn - 1) / bn;
     int64_t W = 0;
     for (int t = 0; t < tiles; ++t) W += en[t] - st[t];
-    const int64_t target = std::max<int64_t>(1, 4 * int64_t(p.num_sms) / ncol);
+    const int64_t target = std::max<int64_t>(1, units_per_sm * int64_t(p.num_sms) / ncol);
     int64_t kc = std::max<int64_t>(4 * int64_t(align), (W + target - 1) / target);
     kc = ((kc + align - 1) / align) * align;
     if (kc > max_kc) kc = max_kc;
@@ -245,8 +246,10 @@ static cudaError_t build_schedules(Plan &p, bool tensor_cores)
         for (int dir = 0; dir < 2; ++dir) {
             std::vector<int64_t> st, en;
             ranges(dir == 0, 64, 64, st, en);
+            // one CTA per SM (shared memory): about one wave of long units,
+            // so the per-unit set-up and the split-K combination are rare
             if ((e = make_schedule(p, p.sched_tc[dir], st, en, 64, sizeof(float), &max_ctas,
-                                   TC_MAX_UNIT)))
+                                   TC_MAX_UNIT, 1)))
                 return e;
         }
         const int64_t npad = ((p.N + 127) / 128) * 128;

@@ -141,6 +141,27 @@ __device__ __forceinline__ void tc_gen_run_tbl(const float *anchor, const ProbeM
     }
 }
 
+// Anchor of the run i_r.. of a probe, or 0 when the run misses the band.
+__device__ __forceinline__ float anchor_of(const float *anchor, const ProbeMeta &m, int64_t i_r)
+{
+    if (i_r + RUN - 1 < m.lo || i_r > m.hi) return 0.f;
+    const int64_t a0 = int64_t(m.lo) & ~int64_t(RUN - 1);
+    return __ldg(&anchor[m.aoff + (i_r - a0) / RUN]);
+}
+
+// The run expanded from an anchor value already in a register.
+__device__ __forceinline__ void tc_expand_run(float v, const ProbeMeta &m, int64_t i_r, const float2 *rs,
+                                              int64_t rbase, float (&v8)[RUN])
+{
+#pragma unroll
+    for (int t = 0; t < RUN; ++t) {
+        const int64_t i = i_r + t;
+        v8[t] = (i >= m.lo && i <= m.hi) ? v : 0.f;
+        const float2 r = rs[i - rbase];
+        v = v * fmaf(m.lam.x, r.x, fmaf(m.lam.x, r.y, m.lam.y * r.x));
+    }
+}
+
 // 16-byte asynchronous global -> shared copy
 __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc)
 {
@@ -151,18 +172,18 @@ __device__ __forceinline__ void cp_async_wait_all()
     asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
-// Packs 8 floats into hi and lo bf16 chunks (hi = rn(v), lo = rn(v - hi)).
+// Packs 8 floats into hi and lo bf16 chunks (hi = rn(v), lo = rn(v - hi)),
+// two values per conversion instruction.
 __device__ __forceinline__ void split_pack(const float (&v)[8], uint4 &hi, uint4 &lo)
 {
     uint32_t h[4], l[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        const __nv_bfloat16 h0 = __float2bfloat16_rn(v[2 * k]);
-        const __nv_bfloat16 h1 = __float2bfloat16_rn(v[2 * k + 1]);
-        const __nv_bfloat16 l0 = __float2bfloat16_rn(v[2 * k] - __bfloat162float(h0));
-        const __nv_bfloat16 l1 = __float2bfloat16_rn(v[2 * k + 1] - __bfloat162float(h1));
-        h[k] = uint32_t(__bfloat16_as_ushort(h0)) | (uint32_t(__bfloat16_as_ushort(h1)) << 16);
-        l[k] = uint32_t(__bfloat16_as_ushort(l0)) | (uint32_t(__bfloat16_as_ushort(l1)) << 16);
+        const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * k], v[2 * k + 1]);
+        const float2 hf = __bfloat1622float2(h2);
+        const __nv_bfloat162 l2 = __floats2bfloat162_rn(v[2 * k] - hf.x, v[2 * k + 1] - hf.y);
+        h[k] = *reinterpret_cast<const uint32_t *>(&h2);
+        l[k] = *reinterpret_cast<const uint32_t *>(&l2);
     }
     hi = make_uint4(h[0], h[1], h[2], h[3]);
     lo = make_uint4(l[0], l[1], l[2], l[3]);
@@ -221,6 +242,36 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(TcArgs a)
     const int nsteps = (wu.k1 - wu.k0) / TC_BK;
     bool ok = true;
 
+    // anchors of a slice: loaded one slice ahead so their latency overlaps the
+    // current slice's arithmetic
+    constexpr int QRUNS = (TILE_R * TC_BK / RUN) / TC_THREADS;
+    auto run_probe = [&](int64_t k0, int q, ProbeMeta &m, int64_t &i_r, int &row, int &chunk) {
+        const int run = tid + q * TC_THREADS;
+        if (FWD) {
+            row = run % TILE_R;
+            chunk = run / TILE_R;
+            m = my_meta;
+            i_r = k0 + int64_t(chunk) * RUN;
+        } else {
+            const int g = run >> 3, t = run & 7;
+            const int pb = g % (TILE_R / 8), kb = g / (TILE_R / 8);
+            const int64_t dk = k0 + kb * 8 + t;
+            m = (dk < wu.k1) ? meta_s[dk - wu.k0] : ProbeMeta{1, 0, 0, make_float2(0.f, 0.f)};
+            i_r = r0 + pb * 8;
+            row = pb * 8 + t;
+            chunk = kb;
+        }
+    };
+    float anc_next[QRUNS];
+    if (nsteps > 0) {
+#pragma unroll
+        for (int q = 0; q < QRUNS; ++q) {
+            ProbeMeta m; int64_t i_r; int row, chunk;
+            run_probe(int64_t(wu.k0), q, m, i_r, row, chunk);
+            anc_next[q] = anchor_of(a.anchor, m, i_r);
+        }
+    }
+
     for (int s = 0; s < nsteps; ++s) {
         const int st = s % TC_STAGES;
         unsigned char *stage = sm + st * L::STAGE_BYTES;
@@ -248,26 +299,32 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(TcArgs a)
             }
         }
         // ---- operand A: Poisson weights ----
+        float anc_cur[QRUNS];
 #pragma unroll
-        for (int q = 0; q < (TILE_R * TC_BK / RUN) / TC_THREADS; ++q) {
-            const int run = tid + q * TC_THREADS;
+        for (int q = 0; q < QRUNS; ++q) anc_cur[q] = anc_next[q];
+        if (s + 1 < nsteps) {
+#pragma unroll
+            for (int q = 0; q < QRUNS; ++q) {
+                ProbeMeta m; int64_t i_r; int row, chunk;
+                run_probe(k0 + TC_BK, q, m, i_r, row, chunk);
+                anc_next[q] = anchor_of(a.anchor, m, i_r);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < QRUNS; ++q) {
+            ProbeMeta m; int64_t i_r; int row, chunk;
+            run_probe(k0, q, m, i_r, row, chunk);
             float v8[RUN];
-            int row, chunk;
             if (FWD) {
                 // row = probe r0 + r, chunk = photon numbers k0 + 8 j .. + 7
-                row = run % TILE_R;
-                chunk = run / TILE_R;
-                tc_gen_run_tbl(a.anchor, my_meta, k0 + int64_t(chunk) * RUN, rinv_s, rbase, v8);
+                tc_expand_run(anc_cur[q], m, i_r, rinv_s, rbase, v8);
             } else {
                 // 8 x 8 block (8 probes x 8 photon numbers) per group of 8
                 // lanes, transposed through shared memory so that one lane
                 // holds 8 consecutive probes of one photon number
-                const int g = run >> 3, t = run & 7;
-                const int pb = g % (TILE_R / 8), kb = g / (TILE_R / 8);
+                const int t = (tid + q * TC_THREADS) & 7;
                 float w8[RUN];
-                const int64_t pk = k0 + kb * 8 + t - wu.k0;   // probe index within the unit
-                const ProbeMeta m = (k0 + kb * 8 + t < wu.k1) ? meta_s[pk] : ProbeMeta{1, 0, 0, make_float2(0.f, 0.f)};
-                tc_gen_run_tbl(a.anchor, m, r0 + pb * 8, rinv_s, rbase, w8);
+                tc_expand_run(anc_cur[q], m, i_r, rinv_s, rbase, w8);
                 float *stg = staging + ((tid >> 3) * 8) * 9;
 #pragma unroll
                 for (int j = 0; j < RUN; ++j) stg[t * 9 + j] = w8[j];
@@ -275,8 +332,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(TcArgs a)
 #pragma unroll
                 for (int j = 0; j < RUN; ++j) v8[j] = stg[j * 9 + t];
                 __syncwarp();
-                row = pb * 8 + t;
-                chunk = kb;
             }
             uint4 hi, lo;
             split_pack(v8, hi, lo);

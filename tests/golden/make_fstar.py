@@ -145,7 +145,7 @@ def main_exact(name: str, seed_iters: int = 100) -> None:
                                      rng.choice(w.M, size=min(w.M, 60), replace=False)]))
     out = {
         "config": w.name,
-        "status": "certified",
+        "status": "certified" if info["converged"] else "provisional",
         "generator": f"workloads.config_{name}()",
         "oracle": "oracle.exact_qp.exact_optimum (active-set KKT solve) seeded by oracle.Problem.fit",
         "f_star": float(f),

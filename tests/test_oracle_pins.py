@@ -473,7 +473,8 @@ def test_exact_kkt_solve_matches_brute_force_and_iterative_solver():
     Th_it, rep, _ = pr.fit(w.P, eps_kkt=1e-12)
     Th, nu, info = exact_qp.exact_optimum(pr.dense_F(), w.P, w.gamma, Th_it)
     f_exact = pr.objective(w.P, Th)
-    assert info["primal_violation"] <= 1e-13 and info["dual_violation"] <= 1e-13
+    assert info["converged"]
+    assert info["primal_violation"] <= 1e-12 and info["dual_violation"] <= 1e-9
     assert f_exact <= rep["f"] * (1 + 1e-13)
     assert f_exact == pytest.approx(rep["f"], rel=1e-11)
     np.testing.assert_allclose(Th.sum(1), 1.0, atol=1e-12)
