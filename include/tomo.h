@@ -209,6 +209,19 @@ tomo_status tomo_hess_diag(tomo_plan_t plan, double *h);
  * Y_i = argmin_{y >= 0, sum y = 1} ||X_i - y||, M rows of N; double. */
 tomo_status tomo_project_simplex(tomo_plan_t plan, const double *X, double *Y);
 
+/* Long-range smoothing (Sec. "Regularisation and smoothing", Eq. smoothing):
+ * Y_{i,n} = mean of X_{j,n} over j in [i - w, i + w], w = floor(i / div),
+ * with the window clipped to [0, M-1] and the mean taken over the rows in it;
+ * rows i < exclude are copied.  The paper uses div = 50 and excludes the
+ * lowest ~100 photon numbers.  X, Y: M x N row-major doubles in device memory
+ * (caller-owned; Y may equal X).  A mean of simplex rows is a simplex row, so
+ * a feasible X gives a feasible Y: the warm start of the stage-2-only refit
+ * (tomo_fit with start_stage = 2).  Computed from double-double column prefix
+ * sums; each output is within a few units in the last place of the exact
+ * window mean.  EINVAL: NULL pointer, exclude < 0 or div <= 0 (or NaN).
+ * Uses plan workspaces: not concurrent with another call on the same plan. */
+tomo_status tomo_smooth(tomo_plan_t plan, const double *X, double *Y, int64_t exclude, double div);
+
 /* KKT residual of App. B for (Theta, G), both M x N device; double. */
 tomo_status tomo_kkt(tomo_plan_t plan, const double *Theta, const double *G,
                      double *kkt_host);

@@ -89,6 +89,7 @@ def lib():
         L.orc_project_simplex_sort.argtypes = [c_ptr, c_i64, c_ptr]
         L.orc_project_simplex_condat.argtypes = [c_ptr, c_i64, c_ptr]
         L.orc_project_rows.argtypes = [c_ptr, c_ptr, c_ptr]
+        L.orc_smooth.argtypes = [c_ptr, c_ptr, c_ptr, c_i64, c_dbl]
         L.orc_fw_gap.restype = c_dbl
         L.orc_fw_gap.argtypes = [c_ptr, c_ptr, c_ptr]
         L.orc_kkt.restype = c_dbl
@@ -239,6 +240,22 @@ class Problem:
 
     def kkt(self, Theta, G) -> float:
         return lib().orc_kkt(self._h, _p(_f64(Theta)), _p(_f64(G)))
+
+    def smooth(self, X, exclude: int = 100, div: float = 50.0) -> np.ndarray:
+        """Long-range smoothing of Eq. smoothing (window floor(i/div), rows
+        below `exclude` unchanged)."""
+        X = _f64(X)
+        Y = np.empty_like(X)
+        lib().orc_smooth(self._h, _p(X), _p(Y), int(exclude), float(div))
+        return Y
+
+    def fit_smoothed(self, P, exclude: int = 100, div: float = 50.0, **opts):
+        """Sec. Regularisation and smoothing: Algorithm 3 from 1/N, long-range
+        smoothing of the result, then stage 2 only from the smoothed POVM."""
+        Th, rep1, _ = self.fit(P, **opts)
+        Ts = self.smooth(Th, exclude, div)
+        Th2, rep2, hist = self.fit(P, Theta0=Ts, start_stage=2, **opts)
+        return Th2, rep1, rep2, Ts
 
     def fw_gap(self, Theta, G) -> float:
         """Upper bound of f(Theta) - f* for a feasible Theta (convexity)."""

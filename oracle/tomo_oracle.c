@@ -477,6 +477,31 @@ ORC_API double orc_fw_gap(const orc_problem *p, const double *Th, const double *
     return s;
 }
 
+/* Long-range smoothing (Eq. smoothing): for i >= exclude,
+ *   Y_{i,n} = mean of X_{j,n} over j in [i - w, i + w], w = floor(i / div),
+ * the window clipped to [0, M-1] (the mean is then over the rows present);
+ * rows i < exclude are copied.  A mean of simplex rows is a simplex row. */
+ORC_API void orc_smooth(const orc_problem *p, const double *X, double *Y, int64_t exclude,
+                        double div)
+{
+    const int64_t M = p->M, N = p->N;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < M; ++i) {
+        if (i < exclude) {
+            for (int64_t n = 0; n < N; ++n) Y[i * N + n] = X[i * N + n];
+            continue;
+        }
+        const int64_t w = (int64_t)floor((double)i / div);
+        const int64_t a = i - w < 0 ? 0 : i - w;
+        const int64_t b = i + w > M - 1 ? M - 1 : i + w;
+        for (int64_t n = 0; n < N; ++n) {
+            double s = 0.0;
+            for (int64_t j = a; j <= b; ++j) s += X[j * N + n];
+            Y[i * N + n] = s / (double)(b - a + 1);
+        }
+    }
+}
+
 /* ---------------------------------------------------------------------- */
 /* Two-stage two-metric projected truncated Newton (Algorithms 1, 2, 3)    */
 /* ---------------------------------------------------------------------- */

@@ -74,6 +74,7 @@ EXPORTS = [
     ("tomo_hvp", c_i32, [c_ptr, c_ptr, c_ptr]),
     ("tomo_hess_diag", c_i32, [c_ptr, c_ptr]),
     ("tomo_project_simplex", c_i32, [c_ptr, c_ptr, c_ptr]),
+    ("tomo_smooth", c_i32, [c_ptr, c_ptr, c_ptr, c_i64, c_dbl]),
     ("tomo_kkt", c_i32, [c_ptr, c_ptr, c_ptr, ctypes.POINTER(c_dbl)]),
     ("tomo_poisson_weights", c_i32, [c_ptr, c_ptr, c_ptr, c_i64, c_ptr]),
     ("tomo_bands", c_i32, [c_ptr, c_ptr, c_ptr]),
@@ -203,6 +204,10 @@ def tomo_hess_diag(h, out):
 
 def tomo_project_simplex(h, X, Y):
     _check(lib().tomo_project_simplex(h, X, Y), "tomo_project_simplex")
+
+
+def tomo_smooth(h, X, Y, exclude=100, div=50.0):
+    _check(lib().tomo_smooth(h, X, Y, int(exclude), float(div)), "tomo_smooth")
 
 
 def tomo_kkt(h, Theta, G) -> float:
@@ -352,6 +357,25 @@ class Plan:
         Y = self._dev_empty(*tuple(X.shape))
         tomo_project_simplex(self._h, _ptr(X), _ptr(Y))
         return Y
+
+    def smooth(self, X, exclude=100, div=50.0, out=None):
+        """Long-range smoothing of Eq. smoothing (window floor(i/div), rows
+        below `exclude` unchanged)."""
+        Y = self._dev_empty(self.M, self.N) if out is None else out
+        tomo_smooth(self._h, _ptr(X), _ptr(Y), exclude, div)
+        return Y
+
+    def fit_smoothed(self, P, exclude=100, div=50.0, **opts):
+        """Sec. Regularisation and smoothing: Algorithm 3 from 1/N, the
+        long-range smoothing of its result (in place), then a stage-2-only
+        refit started from the smoothed POVM.  Returns (Theta, first report,
+        refit report)."""
+        Th, rep1 = self.fit(P, **opts)
+        self.smooth(Th, exclude, div, out=Th)
+        o = dict(opts)
+        o["start_stage"] = 2
+        Th, rep2 = self.fit(P, Th, **o)
+        return Th, rep1, rep2
 
     def kkt(self, Theta, G):
         return tomo_kkt(self._h, _ptr(Theta), _ptr(G))

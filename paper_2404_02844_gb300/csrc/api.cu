@@ -818,6 +818,16 @@ tomo_status tomo_project_simplex(tomo_plan_t plan, const double *X, double *Y)
     return TOMO_OK;
 }
 
+tomo_status tomo_smooth(tomo_plan_t plan, const double *X, double *Y, int64_t exclude, double div)
+{
+    Plan *p = reinterpret_cast<Plan *>(plan);
+    if (!p || !X || !Y) return fail(TOMO_EINVAL, "NULL argument");
+    if (exclude < 0 || !(div > 0.0)) return fail(TOMO_EINVAL, "exclude must be >= 0 and div > 0");
+    CUDA_TRY(launch_smooth(*p, X, Y, exclude, div));
+    CUDA_TRY(cudaStreamSynchronize(p->stream));
+    return TOMO_OK;
+}
+
 tomo_status tomo_kkt(tomo_plan_t plan, const double *Theta, const double *G, double *kkt_host)
 {
     Plan *p = reinterpret_cast<Plan *>(plan);

@@ -478,3 +478,47 @@ def test_exact_kkt_solve_matches_brute_force_and_iterative_solver():
     assert f_exact <= rep["f"] * (1 + 1e-13)
     assert f_exact == pytest.approx(rep["f"], rel=1e-11)
     np.testing.assert_allclose(Th.sum(1), 1.0, atol=1e-12)
+
+
+def test_smoothing_definition_and_closed_forms():
+    """Eq. smoothing: direct window means (numpy), a linear profile is
+    reproduced away from the clipped end, simplex rows stay simplex rows, rows
+    below the exclusion are untouched."""
+    rng = np.random.default_rng(12)
+    M, N = 700, 5
+    pr = oracle.Problem(M, N, np.array([1.0]), 0.0, 0.0)
+    X = workloads.random_feasible_theta(M, N, rng)
+    Y = pr.smooth(X, exclude=100, div=50.0)
+    ref = X.copy()
+    for i in range(100, M):
+        w = i // 50
+        a, b = max(0, i - w), min(M - 1, i + w)
+        ref[i] = X[a:b + 1].mean(axis=0)
+    np.testing.assert_allclose(Y, ref, rtol=1e-13, atol=1e-15)
+    np.testing.assert_allclose(Y.sum(1), 1.0, atol=1e-13)
+    assert Y.min() >= 0.0
+    np.testing.assert_array_equal(Y[:100], X[:100])
+    # linear in i: the symmetric window mean is the centre value (unclipped rows)
+    L = np.outer(np.arange(M, dtype=float), [1.0, -2.0, 0.5, 0.0, 3.0]) + 7.0
+    YL = pr.smooth(L, exclude=0, div=50.0)
+    rows = [i for i in range(M) if i + i // 50 <= M - 1]
+    np.testing.assert_allclose(YL[rows], L[rows], rtol=1e-12)
+
+
+def test_smoothed_refit_returns_to_the_unique_optimum():
+    """Sec. Regularisation and smoothing: the stage-2-only refit starts from
+    the smoothed POVM (feasible: a mean of simplex rows) and, the problem being
+    strictly convex for gamma > 0, converges to the same optimum as the first
+    fit.  A c1-sized case with a short exclusion and divisor (16, 8) so that
+    the smoothing moves most rows; the paper's (100, 50) are parameters."""
+    w = workloads.config_c1()
+    pr = oracle.Problem.from_workload(w)
+    Th1, rep1, _ = pr.fit(w.P, eps_kkt=1e-11, max_newton=800)
+    Th, r1, r2, Ts = pr.fit_smoothed(w.P, exclude=16, div=8.0, eps_kkt=1e-11, max_newton=800)
+    np.testing.assert_allclose(Ts.sum(1), 1.0, atol=1e-13)
+    assert Ts.min() >= 0.0
+    assert np.abs(Ts - Th1).max() > 1e-4      # the smoothing did move the POVM
+    assert r2["iters_s1"] == 0 and r2["iters_s2"] > 0
+    f1, f2, fs = (pr.objective(w.P, T) for T in (Th1, Th, Ts))
+    assert fs > f1 * (1 + 1e-9)                # off the optimum after smoothing
+    assert abs(f2 - f1) <= 1e-9 * f1, (f1, f2)
