@@ -88,7 +88,7 @@ static void free_plan(Plan *p)
     for (void *d : dev)
         if (d) cudaFree(d);
     auto free_sched = [](Schedule &s) {
-        void *sd[] = {s.units, s.tile_first, s.tile_nsplit, s.counters, s.part};
+        void *sd[] = {s.units, s.tile_first, s.tile_nsplit, s.counters, s.part, s.cta_first};
         for (void *d : sd)
             if (d) cudaFree(d);
     };
@@ -145,11 +145,84 @@ static tomo_status check_finite(Plan &p, const double *x, int64_t n, const char 
     return TOMO_OK;
 }
 
-// Work-unit schedules of the band contractions (split-K): the reduction
-// range of every tile (union band of a probe tile, or probe range of a
-// photon-number tile) is cut into units of equal length KC, chosen so that
-// the whole contraction has about four units per SM and column block.
-// Cuts the reduction range of every tile into work units of equal length.
+// Tensor-core schedule, one wave of persistent CTAs: the reduction ranges of
+// all tiles, laid end to end, are cut into `ctas` shares of equal length
+// (multiples of `align`); a share that crosses a tile boundary becomes one
+// unit per tile it touches, and no unit is longer than max_unit (the size of
+// the per-unit tables in shared memory).  CTA c runs its units in order; the
+// units of one tile still combine through the split-K partials, so the
+// result does not depend on which CTA finishes a tile last.
+static cudaError_t make_schedule_tc(Plan &p, Schedule &S, const std::vector<int64_t> &st,
+                                    const std::vector<int64_t> &en, int align, int64_t max_unit,
+                                    int64_t ctas, int64_t *max_ctas)
+{
+    const int tiles = int(st.size());
+    const int bn = band_bn(p.N);
+    const int64_t ncol = (p.N + bn - 1) / bn;
+    int64_t W = 0;
+    for (int t = 0; t < tiles; ++t) W += std::max<int64_t>(0, en[t] - st[t]);
+    if (ctas < 1) ctas = 1;
+    int64_t share = (W + ctas - 1) / ctas;
+    share = std::max<int64_t>(align, ((share + align - 1) / align) * align);
+    std::vector<std::vector<WorkUnit>> per_cta(1);
+    std::vector<int32_t> first(tiles, 0), nsplit(tiles, 0), empty;
+    int64_t room = share;
+    for (int t = 0; t < tiles; ++t) {
+        const int64_t len = en[t] - st[t];
+        if (len <= 0) {
+            empty.push_back(t);
+            continue;
+        }
+        for (int64_t pos = st[t]; pos < en[t];) {
+            if (room == 0) {
+                per_cta.emplace_back();
+                room = share;
+            }
+            const int64_t l = std::min({en[t] - pos, room, max_unit});
+            per_cta.back().push_back(WorkUnit{t, nsplit[t]++, int32_t(pos), int32_t(pos + l)});
+            pos += l;
+            room -= l;
+        }
+    }
+    // an empty reduction still writes its (zero) tile: spread those units
+    // evenly over the CTAs
+    const int64_t nc = int64_t(per_cta.size());
+    for (size_t j = 0; j < empty.size(); ++j) {
+        per_cta[size_t((int64_t(j) * nc) / int64_t(empty.size()))].push_back(WorkUnit{empty[j], 0, 0, 0});
+        nsplit[empty[j]] = 1;
+    }
+    std::vector<WorkUnit> units;
+    std::vector<int32_t> cta_first(1, 0);
+    for (const auto &v : per_cta) {
+        units.insert(units.end(), v.begin(), v.end());
+        cta_first.push_back(int32_t(units.size()));
+    }
+    int64_t slots = 0;
+    for (int t = 0; t < tiles; ++t)
+        if (nsplit[t] > 1) { first[t] = int32_t(slots); slots += nsplit[t]; }
+    cudaError_t e;
+    S.n_units = int(units.size());
+    S.n_ctas = int(cta_first.size()) - 1;
+    if ((e = dalloc(&S.units, int64_t(units.size())))) return e;
+    if ((e = dalloc(&S.tile_first, tiles))) return e;
+    if ((e = dalloc(&S.tile_nsplit, tiles))) return e;
+    if ((e = dalloc(&S.counters, tiles * ncol))) return e;
+    if ((e = dalloc(&S.cta_first, int64_t(cta_first.size())))) return e;
+    if ((e = cudaMalloc(&S.part, std::max<int64_t>(1, slots * ncol) * TILE_R * bn * sizeof(float)))) return e;
+    if ((e = cudaMemcpy(S.units, units.data(), sizeof(WorkUnit) * units.size(), cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(S.tile_first, first.data(), sizeof(int32_t) * tiles, cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(S.tile_nsplit, nsplit.data(), sizeof(int32_t) * tiles, cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(S.cta_first, cta_first.data(), sizeof(int32_t) * cta_first.size(),
+                        cudaMemcpyHostToDevice)) ||
+        (e = cudaMemset(S.counters, 0, sizeof(unsigned) * tiles * ncol)))
+        return e;
+    *max_ctas = std::max<int64_t>(*max_ctas, int64_t(S.n_ctas) * ncol);
+    return cudaSuccess;
+}
+
+// SIMT schedule (split-K): the reduction range of every tile is cut into
+// work units of equal length KC, chosen so that the whole contraction has
+// about `units_per_sm` units per SM and column block; one CTA per unit.
 //   st/en: per-tile [start, end) of the reduction range (empty if equal)
 //   align: unit boundaries are multiples of `align` relative to 0 when
 //          `aligned_start` (start rounded down, end rounded up), else relative
@@ -202,10 +275,10 @@ static cudaError_t make_schedule(Plan &p, Schedule &S, const std::vector<int64_t
     return cudaSuccess;
 }
 
-// Work-unit schedules of the band contractions (split-K): the reduction
-// range of every tile (union band of a probe tile, or probe range of a
-// photon-number tile) is cut into units of equal length, about four units per
-// SM and column block for the whole contraction.
+// Work-unit schedules of the band contractions: the reduction range of every
+// tile (union band of a probe tile, or probe range of a photon-number tile)
+// is cut into split-K units, per unit for the SIMT kernels and per persistent
+// CTA share for the tensor-core kernels.
 static cudaError_t build_schedules(Plan &p, bool tensor_cores)
 {
     std::vector<int32_t> klo(p.fwd_tiles), khi(p.fwd_tiles), dlo(p.adj_tiles), dhi(p.adj_tiles);
@@ -246,10 +319,11 @@ static cudaError_t build_schedules(Plan &p, bool tensor_cores)
         for (int dir = 0; dir < 2; ++dir) {
             std::vector<int64_t> st, en;
             ranges(dir == 0, 64, 64, st, en);
-            // one CTA per SM (shared memory): about one wave of long units,
-            // so the per-unit set-up and the split-K combination are rare
-            if ((e = make_schedule(p, p.sched_tc[dir], st, en, 64, sizeof(float), &max_ctas,
-                                   TC_MAX_UNIT, 1)))
+            // one CTA per SM (shared memory): one wave of persistent CTAs
+            // with equal shares of the reduction work
+            const int64_t ncol = (p.N + band_bn(p.N) - 1) / band_bn(p.N);
+            if ((e = make_schedule_tc(p, p.sched_tc[dir], st, en, 64, TC_MAX_UNIT,
+                                      std::max<int64_t>(1, p.num_sms / ncol), &max_ctas)))
                 return e;
         }
         const int64_t npad = ((p.N + 127) / 128) * 128;
@@ -339,6 +413,7 @@ tomo_status tomo_plan(tomo_plan_t *out, const tomo_desc *d)
     std::memset(p, 0, sizeof(Plan));
     p->M = d->M; p->N = d->N; p->D = d->D;
     p->gamma = d->gamma; p->band_k = d->band_k; p->precision = d->precision;
+    p->cg_f32 = hvp_on_tensor_cores(d->precision);
 
     auto bail = [&](tomo_status s) { free_plan(p); return s; };
 #define PLAN_TRY(expr)                                                                     \
@@ -466,7 +541,7 @@ static tomo_status prof_events(Plan &p, ChunkEvents *out)
 
 static tomo_status cg_chunk(Plan &p, int stage, int count, const ChunkEvents *evs)
 {
-    const double *in = stage == 1 ? p.p : p.u;
+    const double *in = stage == 1 ? p.p : p.u;   // float data when p.cg_f32
     const bool tc = hvp_on_tensor_cores(p.precision);
     // while capturing, profiling events must become event-record nodes
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -477,7 +552,7 @@ static tomo_status cg_chunk(Plan &p, int stage, int count, const ChunkEvents *ev
         if (tc) {
             // tensor cores: the whole Hessian product (forward + adjoint) is
             // timed as the "forward" interval, the adjoint interval is empty
-            CUDA_TRY(launch_hvp_tc(p, in, p.q, true));
+            CUDA_TRY(launch_hvp_tc(p, in, p.q, p.cg_f32, true));
             if (evs) CUDA_TRY(cudaEventRecordWithFlags(evs->ev[c][1], p.stream, evflag));
         } else {
             CUDA_TRY(launch_forward(p, prec_products(p.precision), FWD_STORE, in, p.O, nullptr, true));
@@ -791,7 +866,7 @@ tomo_status tomo_hvp(tomo_plan_t plan, const double *V, double *HV)
     Plan *p = reinterpret_cast<Plan *>(plan);
     if (!p || !V || !HV) return fail(TOMO_EINVAL, "NULL argument");
     if (hvp_on_tensor_cores(p->precision)) {
-        CUDA_TRY(launch_hvp_tc(*p, V, HV, false));
+        CUDA_TRY(launch_hvp_tc(*p, V, HV, false, false));
     } else {
         CUDA_TRY(launch_forward(*p, prec_products(p->precision), FWD_STORE, V, p->O, nullptr, false));
         CUDA_TRY(launch_adjoint(*p, prec_products(p->precision), ADJ_GRAD, p->O, HV, V, false));

@@ -13,6 +13,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "tomo_device.cuh"
 #include "tomo_internal.cuh"
 
@@ -85,14 +87,13 @@ __device__ __forceinline__ int row_argmax(const double (&x)[VPL], int64_t N, int
     return bi < N ? bi : 0;  // a row without any ordered value keeps column 0
 }
 
-template <int VPL>
-__device__ __forceinline__ void load_row(const double *src, int64_t i, int64_t N, int lane,
-                                         double (&v)[VPL])
+template <int VPL, typename T>
+__device__ __forceinline__ void load_row(const T *src, int64_t i, int64_t N, int lane, T (&v)[VPL])
 {
 #pragma unroll
     for (int k = 0; k < VPL; ++k) {
         const int64_t n = lane + 32 * k;
-        v[k] = n < N ? src[i * N + n] : 0.0;
+        v[k] = n < N ? src[i * N + n] : T(0);
     }
 }
 
@@ -239,21 +240,24 @@ __global__ void k_setup1(RowArgs a, int stage, double eps_bar, const double *Th,
 // x = 0, r = -g (free), z = r / diag, p = z; stage 2 also lifts p into
 // u = E p (column m(i) := -sum of the others).
 // ---------------------------------------------------------------------------
-template <int VPL>
+template <int VPL, typename VT>
 __global__ void k_setup2(RowArgs a, int stage, int max_cg, const double *Th, const double *g,
-                         const uint8_t *var, const int32_t *mrow, uint8_t *freem, double *x,
-                         double *r, double *z, double *p, double *u)
+                         const uint8_t *var, const int32_t *mrow, uint8_t *freem, VT *x,
+                         VT *r, VT *z, VT *p, VT *u)
 {
+    constexpr bool F32 = std::is_same<VT, float>::value;
     double rz = 0.0, rr = 0.0;
     const double eps = a.sc->eps;
     ROW_LOOP_BEGIN
     const double diag = stage == 1 ? a.h[i] : 2.0 * a.h[i];
-    double pv[VPL];
-    double psum = 0.0;
+    const float inv = F32 ? float(1.0 / diag) : 0.f;
+    VT pv[VPL];
+    VT psum = 0;
+    float rz_row = 0.f, rr_row = 0.f;
 #pragma unroll
     for (int k = 0; k < VPL; ++k) {
         const int64_t n = lane + 32 * k;
-        pv[k] = 0.0;
+        pv[k] = 0;
         if (n < a.N) {
             const int64_t e = i * a.N + n;
             const double gv = g[e];
@@ -261,17 +265,34 @@ __global__ void k_setup2(RowArgs a, int stage, int max_cg, const double *Th, con
             const bool inI = Th[e] <= eps && gv > 0.0;
             const bool fr = isv && !inI;
             freem[e] = fr;
-            const double rv = fr ? -gv : 0.0;
-            const double zv = fr ? rv / diag : 0.0;
-            x[e] = 0.0;
-            r[e] = rv;
-            z[e] = zv;
-            p[e] = zv;
-            pv[k] = zv;
-            rz += rv * zv;
-            rr += rv * rv;
-            if (stage == 2) psum += zv;
+            if constexpr (F32) {
+                const float rv = fr ? float(-gv) : 0.f;
+                const float zv = rv * inv;
+                x[e] = 0.f;
+                r[e] = rv;
+                z[e] = zv;
+                p[e] = zv;
+                pv[k] = zv;
+                rz_row = fmaf(rv, zv, rz_row);
+                rr_row = fmaf(rv, rv, rr_row);
+                if (stage == 2) psum += zv;
+            } else {
+                const double rv = fr ? -gv : 0.0;
+                const double zv = fr ? rv / diag : 0.0;
+                x[e] = 0.0;
+                r[e] = rv;
+                z[e] = zv;
+                p[e] = zv;
+                pv[k] = zv;
+                rz += rv * zv;
+                rr += rv * rv;
+                if (stage == 2) psum += zv;
+            }
         }
+    }
+    if constexpr (F32) {
+        rz += double(rz_row);
+        rr += double(rr_row);
     }
     if (stage == 2) {
         const int m = mrow[i];
@@ -303,30 +324,34 @@ __global__ void k_setup2(RowArgs a, int stage, int max_cg, const double *Th, con
 // CG: restrict the full Hessian product to the free variables, q = mask(E^T
 // qfull) (stage 2: q_{i,n} = qfull_{i,n} - qfull_{i,m(i)}), and pq = p^T q.
 // ---------------------------------------------------------------------------
-template <int VPL>
+template <int VPL, typename VT>
 __global__ void k_cg_restrict(RowArgs a, int stage, const int32_t *mrow, const uint8_t *freem,
-                              const double *p, double *q)
+                              const VT *p, VT *q)
 {
+    constexpr bool F32 = std::is_same<VT, float>::value;
     if (a.sc->cg_active == 0) return;
     double pq = 0.0;
     ROW_LOOP_BEGIN
-    double qv[VPL];
+    VT qv[VPL];
     load_row<VPL>(q, i, a.N, lane, qv);
-    double qm = 0.0;
+    VT qm = 0;
     if (stage == 2) {
         const int m = mrow[i];
         qm = __shfl_sync(0xffffffffu, qv[(m / 32) % VPL], m % 32);
     }
+    float pq_row = 0.f;
 #pragma unroll
     for (int k = 0; k < VPL; ++k) {
         const int64_t n = lane + 32 * k;
         if (n < a.N) {
             const int64_t e = i * a.N + n;
-            const double v = freem[e] ? qv[k] - qm : 0.0;
+            const VT v = freem[e] ? qv[k] - qm : VT(0);
             q[e] = v;
-            pq += p[e] * v;
+            if constexpr (F32) pq_row = fmaf(p[e], v, pq_row);
+            else pq += p[e] * v;
         }
     }
+    if constexpr (F32) pq += double(pq_row);
     ROW_LOOP_END
     double v[1] = {pq};
     DevScalars *sc = a.sc;
@@ -341,26 +366,49 @@ __global__ void k_cg_restrict(RowArgs a, int stage, const int32_t *mrow, const u
 }
 
 // x += alpha p, r -= alpha q, z = r / diag (free), with r.z and r.r; warp per
-// row (the diagonal is one value per row).
-__global__ void k_cg_update_xr(RowArgs a, int stage, const uint8_t *freem, const double *p,
-                               const double *q, double *x, double *r, double *z)
+// row (the diagonal is one value per row).  Float vectors scale by the
+// row's reciprocal diagonal and sum each row in float before the double
+// accumulation.
+template <typename VT>
+__global__ void k_cg_update_xr(RowArgs a, int stage, const uint8_t *freem, const VT *p,
+                               const VT *q, VT *x, VT *r, VT *z)
 {
+    constexpr bool F32 = std::is_same<VT, float>::value;
     if (a.sc->cg_active == 0) return;
     const double al = a.sc->alpha;
+    const float alf = float(al);
     const double scale = stage == 1 ? 1.0 : 2.0;
     double rz = 0.0, rr = 0.0;
     ROW_LOOP_BEGIN
     const double diag = scale * a.h[i];
-    for (int64_t n = lane; n < a.N; n += 32) {
-        const int64_t e = i * a.N + n;
-        const double xv = x[e] + al * p[e];
-        const double rv = r[e] - al * q[e];
-        const double zv = freem[e] ? rv / diag : 0.0;
-        x[e] = xv;
-        r[e] = rv;
-        z[e] = zv;
-        rz += rv * zv;
-        rr += rv * rv;
+    if constexpr (F32) {
+        const float inv = float(1.0 / diag);
+        float rz_row = 0.f, rr_row = 0.f;
+        for (int64_t n = lane; n < a.N; n += 32) {
+            const int64_t e = i * a.N + n;
+            const float xv = fmaf(alf, p[e], x[e]);
+            const float rv = fmaf(-alf, q[e], r[e]);
+            const float zv = freem[e] ? rv * inv : 0.f;
+            x[e] = xv;
+            r[e] = rv;
+            z[e] = zv;
+            rz_row = fmaf(rv, zv, rz_row);
+            rr_row = fmaf(rv, rv, rr_row);
+        }
+        rz += double(rz_row);
+        rr += double(rr_row);
+    } else {
+        for (int64_t n = lane; n < a.N; n += 32) {
+            const int64_t e = i * a.N + n;
+            const double xv = x[e] + al * p[e];
+            const double rv = r[e] - al * q[e];
+            const double zv = freem[e] ? rv / diag : 0.0;
+            x[e] = xv;
+            r[e] = rv;
+            z[e] = zv;
+            rz += rv * zv;
+            rr += rv * rv;
+        }
     }
     ROW_LOOP_END
     double v[2] = {rz, rr};
@@ -375,22 +423,22 @@ __global__ void k_cg_update_xr(RowArgs a, int stage, const uint8_t *freem, const
 }
 
 // p = z + beta p; stage 2 also u = E p.
-template <int VPL>
-__global__ void k_cg_update_p(RowArgs a, int stage, const int32_t *mrow, const double *z,
-                              double *p, double *u)
+template <int VPL, typename VT>
+__global__ void k_cg_update_p(RowArgs a, int stage, const int32_t *mrow, const VT *z,
+                              VT *p, VT *u)
 {
     if (a.sc->cg_active == 0) return;
-    const double be = a.sc->beta;
+    const VT be = VT(a.sc->beta);
     ROW_LOOP_BEGIN
-    double pv[VPL];
-    double psum = 0.0;
+    VT pv[VPL];
+    VT psum = 0;
 #pragma unroll
     for (int k = 0; k < VPL; ++k) {
         const int64_t n = lane + 32 * k;
-        pv[k] = 0.0;
+        pv[k] = 0;
         if (n < a.N) {
             const int64_t e = i * a.N + n;
-            const double v = z[e] + be * p[e];
+            const VT v = z[e] + be * p[e];
             p[e] = v;
             pv[k] = v;
             psum += v;
@@ -398,7 +446,7 @@ __global__ void k_cg_update_p(RowArgs a, int stage, const int32_t *mrow, const d
     }
     if (stage == 2) {
         const int m = mrow[i];
-        const double pm = __shfl_sync(0xffffffffu, pv[(m / 32) % VPL], m % 32);
+        const VT pm = __shfl_sync(0xffffffffu, pv[(m / 32) % VPL], m % 32);
         psum = warp_sum(psum) - pm;
 #pragma unroll
         for (int k = 0; k < VPL; ++k) {
@@ -411,8 +459,9 @@ __global__ void k_cg_update_p(RowArgs a, int stage, const int32_t *mrow, const d
 
 // Newton direction: CG solution on the free variables, -g/diag on I, 0 on
 // non-variables; g^T dir decides whether the scaled gradient replaces it.
+template <typename VT>
 __global__ void k_direction(RowArgs a, int stage, const uint8_t *var, const uint8_t *freem,
-                            const double *x, const double *g, double *dir)
+                            const VT *x, const double *g, double *dir)
 {
     const double scale = stage == 1 ? 1.0 : 2.0;
     double gd = 0.0;
@@ -422,7 +471,7 @@ __global__ void k_direction(RowArgs a, int stage, const uint8_t *var, const uint
         const int64_t e = i * a.N + n;
         double d;
         if (!var[e]) d = 0.0;
-        else if (freem[e]) d = x[e];
+        else if (freem[e]) d = double(x[e]);
         else d = -g[e] / diag;
         dir[e] = d;
         gd += g[e] * d;
@@ -637,6 +686,21 @@ static unsigned elem_grid(const Plan &p, int64_t n)
     return unsigned(g);
 }
 
+#define VPL_DISPATCH_T(N, KERNEL, VT, GRID, ...)                                            \
+    do {                                                                                    \
+        const int64_t _n = (N);                                                             \
+        if (_n <= 32) KERNEL<1, VT><<<GRID, ROW_WARPS * 32, 0, p.stream>>>(__VA_ARGS__);     \
+        else if (_n <= 64) KERNEL<2, VT><<<GRID, ROW_WARPS * 32, 0, p.stream>>>(__VA_ARGS__); \
+        else if (_n <= 128) KERNEL<4, VT><<<GRID, ROW_WARPS * 32, 0, p.stream>>>(__VA_ARGS__); \
+        else if (_n <= 256) KERNEL<8, VT><<<GRID, ROW_WARPS * 32, 0, p.stream>>>(__VA_ARGS__); \
+        else if (_n <= 512) KERNEL<16, VT><<<GRID, ROW_WARPS * 32, 0, p.stream>>>(__VA_ARGS__); \
+        else KERNEL<32, VT><<<GRID, ROW_WARPS * 32, 0, p.stream>>>(__VA_ARGS__);             \
+        count_launch();                                                                     \
+    } while (0)
+
+// CG vectors: float in the tensor-core form, double otherwise (same buffers)
+#define CGV(ptr) reinterpret_cast<float *>(ptr)
+
 #define VPL_DISPATCH(N, KERNEL, GRID, ...)                                                  \
     do {                                                                                    \
         const int64_t _n = (N);                                                             \
@@ -703,23 +767,34 @@ cudaError_t launch_setup1(Plan &p, int stage, double eps_bar)
 cudaError_t launch_setup2(Plan &p, int stage, int max_cg)
 {
     RowArgs a = row_args(p);
-    VPL_DISPATCH(p.N, k_setup2, row_grid(p), a, stage, max_cg, p.Th, p.g, p.var, p.mrow,
-                 p.freem, p.x, p.r, p.z, p.p, p.u);
+    if (p.cg_f32)
+        VPL_DISPATCH_T(p.N, k_setup2, float, row_grid(p), a, stage, max_cg, p.Th, p.g, p.var, p.mrow,
+                       p.freem, CGV(p.x), CGV(p.r), CGV(p.z), CGV(p.p), CGV(p.u));
+    else
+        VPL_DISPATCH_T(p.N, k_setup2, double, row_grid(p), a, stage, max_cg, p.Th, p.g, p.var, p.mrow,
+                       p.freem, p.x, p.r, p.z, p.p, p.u);
     return cudaGetLastError();
 }
 
 cudaError_t launch_cg_restrict(Plan &p, int stage)
 {
     RowArgs a = row_args(p);
-    VPL_DISPATCH(p.N, k_cg_restrict, row_grid(p), a, stage, p.mrow, p.freem, p.p, p.q);
+    if (p.cg_f32)
+        VPL_DISPATCH_T(p.N, k_cg_restrict, float, row_grid(p), a, stage, p.mrow, p.freem, CGV(p.p), CGV(p.q));
+    else
+        VPL_DISPATCH_T(p.N, k_cg_restrict, double, row_grid(p), a, stage, p.mrow, p.freem, p.p, p.q);
     return cudaGetLastError();
 }
 
 cudaError_t launch_cg_update_xr(Plan &p, int stage)
 {
     RowArgs a = row_args(p);
-    k_cg_update_xr<<<row_grid(p), ROW_WARPS * 32, 0, p.stream>>>(a, stage, p.freem, p.p, p.q,
-                                                                 p.x, p.r, p.z);
+    if (p.cg_f32)
+        k_cg_update_xr<float><<<row_grid(p), ROW_WARPS * 32, 0, p.stream>>>(
+            a, stage, p.freem, CGV(p.p), CGV(p.q), CGV(p.x), CGV(p.r), CGV(p.z));
+    else
+        k_cg_update_xr<double><<<row_grid(p), ROW_WARPS * 32, 0, p.stream>>>(a, stage, p.freem, p.p, p.q,
+                                                                         p.x, p.r, p.z);
     count_launch();
     return cudaGetLastError();
 }
@@ -727,15 +802,22 @@ cudaError_t launch_cg_update_xr(Plan &p, int stage)
 cudaError_t launch_cg_update_p(Plan &p, int stage)
 {
     RowArgs a = row_args(p);
-    VPL_DISPATCH(p.N, k_cg_update_p, row_grid(p), a, stage, p.mrow, p.z, p.p, p.u);
+    if (p.cg_f32)
+        VPL_DISPATCH_T(p.N, k_cg_update_p, float, row_grid(p), a, stage, p.mrow, CGV(p.z), CGV(p.p), CGV(p.u));
+    else
+        VPL_DISPATCH_T(p.N, k_cg_update_p, double, row_grid(p), a, stage, p.mrow, p.z, p.p, p.u);
     return cudaGetLastError();
 }
 
 cudaError_t launch_direction(Plan &p, int stage)
 {
     RowArgs a = row_args(p);
-    k_direction<<<row_grid(p), ROW_WARPS * 32, 0, p.stream>>>(a, stage, p.var, p.freem, p.x,
-                                                              p.g, p.dir);
+    if (p.cg_f32)
+        k_direction<float><<<row_grid(p), ROW_WARPS * 32, 0, p.stream>>>(a, stage, p.var, p.freem, CGV(p.x),
+                                                                         p.g, p.dir);
+    else
+        k_direction<double><<<row_grid(p), ROW_WARPS * 32, 0, p.stream>>>(a, stage, p.var, p.freem, p.x,
+                                                                          p.g, p.dir);
     count_launch();
     return cudaGetLastError();
 }

@@ -60,6 +60,7 @@ struct TcArgs {
     const float *anchor;
     const float2 *rinv2;
     const WorkUnit *units;
+    const int32_t *cta_first;     // units of CTA c: cta_first[c] .. cta_first[c+1]-1
     const int32_t *tile_first;
     const int32_t *tile_nsplit;
     unsigned int *counters;
@@ -72,9 +73,11 @@ struct TcArgs {
     // forward output: transposed bf16 hi/lo copy of O (pitch opitch)
     __nv_bfloat16 *o_hi, *o_lo;
     int64_t opitch;
-    // adjoint output: q = 2 Z + 2 gamma L u (double, M x N)
-    double *q;
-    const double *u;
+    // adjoint output: q = 2 Z + 2 gamma L u (M x N), in float when vec_f32
+    // (the CG vectors of the tensor-core form), else in double
+    void *q;
+    const void *u;
+    int vec_f32;
     double gamma;
 };
 
@@ -206,10 +209,31 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(TcArgs a)
     float2 *rinv_s = reinterpret_cast<float2 *>(reinterpret_cast<unsigned char *>(meta_s) + L::META_BYTES);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const WorkUnit wu = a.units[blockIdx.x];
+    if (warp == 0) {
+        tc::tmem_alloc(tmem_holder, L::TMEM_COLS);
+        tc::tmem_relinquish();
+    }
+    if (tid == 0) {
+        for (int s = 0; s < TC_STAGES; ++s) tc::mbar_init(&bars[s], 1);
+        tc::mbar_fence_init();
+    }
+    tc::tc_fence_before_sync();
+    __syncthreads();
+    tc::tc_fence_after_sync();
+    const uint32_t tmem = *tmem_holder;
+    const int64_t n0 = int64_t(blockIdx.y) * BN;
+    bool ok = true;
+    // pipeline steps issued by this CTA so far (stage and mbarrier phase of
+    // every step follow from it across units)
+    uint32_t gstep = 0;
+    __shared__ int last;
+
+    // the CTA's units, in order (one wave of persistent CTAs)
+    const int u_end = a.cta_first[blockIdx.x + 1];
+    for (int ui = a.cta_first[blockIdx.x]; ui < u_end; ++ui) {
+    const WorkUnit wu = a.units[ui];
     const int tile = wu.tile;
     const int64_t r0 = int64_t(tile) * TILE_R;
-    const int64_t n0 = int64_t(blockIdx.y) * BN;
 
     // unit tables: the 1/(i+1) pairs of every photon number the unit touches
     // (forward: the unit's photon range; adjoint: the tile's photon range)
@@ -224,23 +248,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(TcArgs a)
         for (int64_t k = tid; k < int64_t(wu.k1 - wu.k0); k += TC_THREADS) meta_s[k] = load_meta(a, wu.k0 + k);
     // forward: every thread generates the runs of one probe (row tid % 128)
     const ProbeMeta my_meta = FWD ? load_meta(a, r0 + (tid % TILE_R)) : ProbeMeta{1, 0, 0, make_float2(0.f, 0.f)};
-
-    if (warp == 0) {
-        tc::tmem_alloc(tmem_holder, L::TMEM_COLS);
-        tc::tmem_relinquish();
-    }
-    if (tid == 0) {
-        for (int s = 0; s < TC_STAGES; ++s) tc::mbar_init(&bars[s], 1);
-        tc::mbar_fence_init();
-    }
-    tc::tc_fence_before_sync();
     __syncthreads();
-    tc::tc_fence_after_sync();
-    const uint32_t tmem = *tmem_holder;
 
     constexpr uint32_t IDESC = tc::idesc_bf16_f32(TILE_R, BN);
     const int nsteps = (wu.k1 - wu.k0) / TC_BK;
-    bool ok = true;
 
     // anchors of a slice: loaded one slice ahead so their latency overlaps the
     // current slice's arithmetic
@@ -273,15 +284,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(TcArgs a)
     }
 
     for (int s = 0; s < nsteps; ++s) {
-        const int st = s % TC_STAGES;
+        const uint32_t g = gstep + uint32_t(s);
+        const int st = int(g % TC_STAGES);
         unsigned char *stage = sm + st * L::STAGE_BYTES;
         unsigned char *A_hi = stage;
         unsigned char *A_lo = stage + L::A_BYTES;                       // SPLIT == 3 only
         unsigned char *B_hi = stage + L::NPART * L::A_BYTES;
         unsigned char *B_lo = B_hi + L::B_BYTES;                        // SPLIT == 3 only
-        if (s >= TC_STAGES) {
-            // the MMAs issued TC_STAGES steps ago read this stage
-            if (!tc::mbar_wait_bounded(&bars[st], uint32_t((s / TC_STAGES) - 1) & 1u, TC_WAIT_LIMIT))
+        if (g >= TC_STAGES) {
+            // the MMAs issued TC_STAGES steps ago (maybe by the previous unit)
+            // read this stage
+            if (!tc::mbar_wait_bounded(&bars[st], ((g / TC_STAGES) - 1) & 1u, TC_WAIT_LIMIT))
                 ok = false;
         }
         const int64_t k0 = int64_t(wu.k0) + int64_t(s) * TC_BK;
@@ -360,10 +373,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(TcArgs a)
         }
     }
     if (nsteps > 0) {
-        const int s = nsteps - 1;
-        if (!tc::mbar_wait_bounded(&bars[s % TC_STAGES], uint32_t(s / TC_STAGES) & 1u, TC_WAIT_LIMIT))
+        const uint32_t g = gstep + uint32_t(nsteps - 1);
+        if (!tc::mbar_wait_bounded(&bars[g % TC_STAGES], (g / TC_STAGES) & 1u, TC_WAIT_LIMIT))
             ok = false;
     }
+    gstep += uint32_t(nsteps);
     tc::tc_fence_after_sync();
 
     // ---- epilogue: tensor memory -> registers ----
@@ -377,7 +391,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(TcArgs a)
     const int nsplit = a.tile_nsplit[tile];
     const int ncb = gridDim.y;
     const int64_t tile_elems = int64_t(TILE_R) * BN;
-    __shared__ int last;
 
     float acc[COLS_PER_WARP];
     if (active) {
@@ -441,26 +454,57 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(TcArgs a)
                     }
                 }
             }
-        } else if (grow < a.M) {
-            const double g2 = 2.0 * a.gamma;
+        }
+    }
+    if (!FWD && owner) {
+        // q = 2 Z + 2 gamma L u through a shared-memory copy of the tile (the
+        // stage buffers: this unit's MMAs and copies are complete), so that
+        // the reads of u and the writes of q run along rows (coalesced)
+        constexpr int LD = BN + 1;
+        float *tile_s = reinterpret_cast<float *>(sm);
+        if (active) {
 #pragma unroll
-            for (int c = 0; c < COLS_PER_WARP; ++c) {
-                const int64_t n = n0 + col0 + c;
-                if (n < a.N) {
-                    const int64_t k = grow * a.N + n;
-                    double lx = 0.0;
-                    if (g2 != 0.0) {
-                        const double xi = a.u[k];
-                        if (grow < a.M - 1) lx += xi - a.u[k + a.N];
-                        if (grow > 0) lx += xi - a.u[k - a.N];
-                    }
-                    a.q[k] = 2.0 * double(acc[c]) + g2 * lx;
+            for (int c = 0; c < COLS_PER_WARP; ++c) tile_s[row * LD + col0 + c] = acc[c];
+        }
+        __syncthreads();
+        const double g2 = 2.0 * a.gamma;
+        const float g2f = float(g2);
+        for (int e = tid; e < TILE_R * BN; e += TC_THREADS) {
+            const int rr = e / BN, cc = e - (e / BN) * BN;
+            const int64_t grow = r0 + rr, n = n0 + cc;
+            if (grow >= a.M || n >= a.N) continue;
+            const int64_t k = grow * a.N + n;
+            const float z = tile_s[rr * LD + cc];
+            if (a.vec_f32) {
+                const float *u = static_cast<const float *>(a.u);
+                float lx = 0.f;
+                if (g2f != 0.f) {
+                    const float xi = u[k];
+                    if (grow < a.M - 1) lx += xi - u[k + a.N];
+                    if (grow > 0) lx += xi - u[k - a.N];
                 }
+                static_cast<float *>(a.q)[k] = fmaf(g2f, lx, 2.f * z);
+            } else {
+                const double *u = static_cast<const double *>(a.u);
+                double lx = 0.0;
+                if (g2 != 0.0) {
+                    const double xi = u[k];
+                    if (grow < a.M - 1) lx += xi - u[k + a.N];
+                    if (grow > 0) lx += xi - u[k - a.N];
+                }
+                static_cast<double *>(a.q)[k] = 2.0 * double(z) + g2 * lx;
             }
         }
     }
+    // the next unit's first MMA overwrites the accumulator and its tables
+    // replace these: every thread is past its tensor-memory loads.  A wait
+    // that gave up in any thread ends the CTA's work (uniformly).
     tc::tc_fence_before_sync();
-    __syncthreads();
+    if (__syncthreads_or(ok ? 0 : 1)) {
+        ok = false;
+        break;
+    }
+    }  // units
     if (warp == 0) tc::tmem_dealloc(tmem, L::TMEM_COLS);
     if (!ok && tid == 0) atomicExch(a.err, 1);
 }
@@ -470,25 +514,26 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(TcArgs a)
 // pitch = padded M), through a 32 x 32 shared-memory tile so that both the
 // reads and the writes are coalesced.  Gated like the CG kernels.
 // ----------------------------------------------------------------------------
-__global__ void k_transpose_split(const int32_t *gate, int64_t M, int64_t N, const double *u,
+template <typename VT>
+__global__ void k_transpose_split(const int32_t *gate, int64_t M, int64_t N, const VT *u,
                                   __nv_bfloat16 *t_hi, __nv_bfloat16 *t_lo, int64_t pitch)
 {
     if (gate && *gate == 0) return;
-    __shared__ double tile[32][33];
+    __shared__ VT tile[32][33];
     const int64_t i0 = int64_t(blockIdx.x) * 32, nb = int64_t(blockIdx.y) * 32;
     for (int r = threadIdx.y; r < 32; r += blockDim.y) {
         const int64_t i = i0 + r, n = nb + threadIdx.x;
-        tile[r][threadIdx.x] = (i < M && n < N) ? u[i * N + n] : 0.0;
+        tile[r][threadIdx.x] = (i < M && n < N) ? u[i * N + n] : VT(0);
     }
     __syncthreads();
     for (int r = threadIdx.y; r < 32; r += blockDim.y) {
         const int64_t n = nb + r, i = i0 + threadIdx.x;
         if (n < N && i < M) {
             // hi = bf16(u), lo = bf16(u - hi)
-            const double v = tile[threadIdx.x][r];
+            const VT v = tile[threadIdx.x][r];
             const __nv_bfloat16 h = __float2bfloat16_rn(float(v));
             t_hi[n * pitch + i] = h;
-            t_lo[n * pitch + i] = __float2bfloat16_rn(float(v - double(__bfloat162float(h))));
+            t_lo[n * pitch + i] = __float2bfloat16_rn(float(v - VT(__bfloat162float(h))));
         }
     }
 }
@@ -505,7 +550,7 @@ static cudaError_t launch_tc_t(Plan &p, const TcArgs &a)
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (cfg != cudaSuccess) return cfg;
     const Schedule &S = p.sched_tc[FWD ? 0 : 1];
-    dim3 grid(unsigned(S.n_units), unsigned((p.N + BN - 1) / BN));
+    dim3 grid(unsigned(S.n_ctas), unsigned((p.N + BN - 1) / BN));
     kern<<<grid, TC_THREADS, smem, p.stream>>>(a);
     count_launch();
     return cudaGetLastError();
@@ -528,7 +573,8 @@ static TcArgs tc_args(Plan &p, bool fwd, const int32_t *gate)
     a.lam2 = p.lam_f2; a.lo = p.lo; a.hi = p.hi; a.aoff = p.aoff;
     a.anchor = p.anchor_f; a.rinv2 = p.ratio_inv_f2;
     const Schedule &S = p.sched_tc[fwd ? 0 : 1];
-    a.units = S.units; a.tile_first = S.tile_first; a.tile_nsplit = S.tile_nsplit;
+    a.units = S.units; a.cta_first = S.cta_first;
+    a.tile_first = S.tile_first; a.tile_nsplit = S.tile_nsplit;
     a.counters = S.counters; a.part = reinterpret_cast<float *>(S.part);
     a.gate = gate;
     a.err = &p.sc->tc_err;
@@ -536,7 +582,7 @@ static TcArgs tc_args(Plan &p, bool fwd, const int32_t *gate)
     a.b_lo = fwd ? p.ut_lo : p.ot_lo;
     a.bpitch = fwd ? p.ut_pitch : p.ot_pitch;
     a.o_hi = p.ot_hi; a.o_lo = p.ot_lo; a.opitch = p.ot_pitch;
-    a.q = nullptr; a.u = nullptr;
+    a.q = nullptr; a.u = nullptr; a.vec_f32 = 0;
     a.gamma = p.gamma;
     return a;
 }
@@ -544,11 +590,16 @@ static TcArgs tc_args(Plan &p, bool fwd, const int32_t *gate)
 // HV = 2 F^T (F V) + 2 gamma L V on the tensor cores (three launches: the
 // transposed split copy of V, the forward tile product, the adjoint tile
 // product with the smoothness term).
-cudaError_t launch_hvp_tc(Plan &p, const double *V, double *HV, bool gated)
+cudaError_t launch_hvp_tc(Plan &p, const void *V, void *HV, bool vec_f32, bool gated)
 {
     const int32_t *gate = gated ? &p.sc->cg_active : nullptr;
     dim3 tb(32, 8), tg(unsigned((p.M + 31) / 32), unsigned((p.N + 31) / 32));
-    k_transpose_split<<<tg, tb, 0, p.stream>>>(gate, p.M, p.N, V, p.ut_hi, p.ut_lo, p.ut_pitch);
+    if (vec_f32)
+        k_transpose_split<float><<<tg, tb, 0, p.stream>>>(gate, p.M, p.N, static_cast<const float *>(V),
+                                                           p.ut_hi, p.ut_lo, p.ut_pitch);
+    else
+        k_transpose_split<double><<<tg, tb, 0, p.stream>>>(gate, p.M, p.N, static_cast<const double *>(V),
+                                                            p.ut_hi, p.ut_lo, p.ut_pitch);
     count_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -557,6 +608,7 @@ cudaError_t launch_hvp_tc(Plan &p, const double *V, double *HV, bool gated)
     TcArgs b = tc_args(p, false, gate);
     b.q = HV;
     b.u = V;
+    b.vec_f32 = vec_f32 ? 1 : 0;
     return launch_tc<false>(p, b);
 }
 

@@ -60,12 +60,16 @@ struct Schedule {
     unsigned int *counters; // device, per (tile, column block)
     void *part;             // device partial tiles
     int n_units;
+    // tensor-core schedules: CTA c runs units cta_first[c] .. cta_first[c+1]-1
+    int32_t *cta_first;     // device, n_ctas + 1 (null for the SIMT schedules)
+    int n_ctas;
 };
 
 struct Plan {
     int64_t M, N, D;
     double gamma, band_k;
     int precision;
+    bool cg_f32;       // CG vectors x, r, z, p, u, q held as float (tensor-core form)
     cudaStream_t stream;
     bool own_stream;
     int device;
@@ -169,7 +173,8 @@ inline int prec_gradient(int precision)
 inline bool hvp_on_tensor_cores(int precision) { return precision == TOMO_PREC_TC; }
 
 // tc_band.cu
-cudaError_t launch_hvp_tc(Plan &p, const double *V, double *HV, bool gated);
+// V, HV: float when vec_f32 (the CG vectors of the tensor-core form), else double
+cudaError_t launch_hvp_tc(Plan &p, const void *V, void *HV, bool vec_f32, bool gated);
 size_t tc_smem_bytes(int bn);
 
 // records a failure message for tomo_last_error (api.cu)
