@@ -8,9 +8,10 @@ A step is one full two-stage solve (Algorithm 3) from Theta^(0) = 1/N until the
 objective is within 1e-8 (relative) of the optimum certified by the FP64
 oracle (tests/golden/fstar_c2.json, written by tests/golden/make_fstar.py).
 The chosen form runs the CG Hessian products on the tensor cores (tcgen05,
-bf16 hi/lo split, f32 accumulation), the line-search products in FP32, the
-gradient, residual and every reduction in FP64; the plain FP64 GPU solver is
-timed beside it.  Prints one JSON line.
+bf16 hi/lo split, f32 accumulation) with float CG vectors, the gradient and
+line-search products as FP32 SIMT contractions, and keeps Theta, the residual
+(refreshed by an FP64 product every 8 Newton iterations) and the reductions
+in FP64; the plain FP64 GPU solver is timed beside it.  Prints one JSON line.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -129,7 +130,8 @@ def max_over_ranks(world, x: float) -> float:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -182,7 +184,7 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
     ap.add_argument("--plain-sample-iters", type=int, default=20)
-    ap.add_argument("--cpu-sample-iters", type=int, default=8)
+    ap.add_argument("--cpu-sample-iters", type=int, default=40)
     args = ap.parse_args()
     world, rank, local = dist_init()
     if args.impl == "reference":
@@ -344,7 +346,7 @@ def main():
             "data": "synthetic (seeded PCG64; stands in for the paper's experimental data)",
             "config": {"workload": WORKLOAD, "global_batch": world, "seq_len": M,
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                       "form": "chosen: tensor-core CG Hessian products (bf16 hi/lo x3), FP32 line-search products and gradient, FP64 residual refresh/objective/reductions",
+                       "form": "chosen: tensor-core CG Hessian products (bf16 hi/lo x3) with float CG vectors, FP32 line-search products and gradient, FP64 Theta/residual refresh/objective/reductions",
                        "l2": "flushed (512 MB write) before every timed solve"},
             "time_to_tolerance_s": ttt,
             "rel_gap": gap,

@@ -61,10 +61,12 @@ typedef enum {
  *         but the gradient F^T R is contracted in double.
  *   TC:   the CG Hessian products run on the tensor cores (tcgen05.mma,
  *         bf16 operands split into hi + lo parts, three products per slice,
- *         f32 accumulation in tensor memory: ~16 significant bits); the
- *         line-search products F s and the gradient F^T R are contracted in
- *         float (the Armijo test needs float-grade F s); residual refreshes,
- *         the objective and every reduction in double. */
+ *         f32 accumulation in tensor memory: ~16 significant bits) and the
+ *         CG vectors (x, r, z, p) are float, their dot products summed per
+ *         row in float and across rows in double; the line-search products
+ *         F s and the gradient F^T R are contracted in float (the Armijo
+ *         test needs float-grade F s); Theta, the gradient, residual
+ *         refreshes, the objective and every other reduction in double. */
 typedef enum {
     TOMO_PREC_FP64 = 0,
     TOMO_PREC_FP32 = 1,

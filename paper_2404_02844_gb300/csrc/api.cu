@@ -81,7 +81,7 @@ static void free_plan(Plan *p)
 {
     if (!p) return;
     void *dev[] = {p->lam, p->lo, p->hi, p->aoff, p->anchor, p->anchor_f, p->ratio_inv,
-                   p->ratio_inv_f2, p->lam_f2, p->fwd_klo, p->fwd_khi, p->adj_dlo, p->adj_dhi, p->h,
+                   p->ratio_inv_f2, p->lam_f2, p->fwd_klo, p->fwd_khi, p->adj_dlo, p->adj_dhi, p->h, p->hinv_f,
                    p->Th, p->trial, p->s, p->G, p->g, p->x, p->r, p->z, p->p, p->u, p->q,
                    p->dir, p->R, p->Rt, p->O, p->Pbuf, p->Xbuf, p->freem, p->var, p->mrow,
                    p->partials, p->sc, p->idx_buf, p->val_buf};
@@ -452,6 +452,7 @@ tomo_status tomo_plan(tomo_plan_t *out, const tomo_desc *d)
     PLAN_TRY(dalloc(&p->adj_dlo, p->adj_tiles));
     PLAN_TRY(dalloc(&p->adj_dhi, p->adj_tiles));
     PLAN_TRY(dalloc(&p->h, M));
+    PLAN_TRY(dalloc(&p->hinv_f, 2 * M));
     double **mn_bufs[] = {&p->Th, &p->trial, &p->s, &p->G, &p->g, &p->x, &p->r,
                           &p->z, &p->p, &p->u, &p->q, &p->dir};
     for (double **b : mn_bufs) PLAN_TRY(dalloc(b, MN));

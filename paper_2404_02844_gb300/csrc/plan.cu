@@ -169,7 +169,7 @@ __device__ float weight_from_anchor_f(int64_t d, int64_t i, const float2 *lam2,
 __global__ void k_hess_diag(int64_t M, double gamma, const double *lam, const int32_t *lo,
                             const int32_t *hi, const int64_t *aoff, const double *anc,
                             const double *rinv, const int32_t *dlo, const int32_t *dhi,
-                            double *h)
+                            double *h, float *hinv)
 {
     const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
     if (i >= M) return;
@@ -180,7 +180,12 @@ __global__ void k_hess_diag(int64_t M, double gamma, const double *lam, const in
         s += f * f;
     }
     const double lii = double((i > 0) + (i < M - 1));
-    h[i] = 2.0 * s + 2.0 * gamma * lii;
+    const double hv = 2.0 * s + 2.0 * gamma * lii;
+    h[i] = hv;
+    // float reciprocals of the stage-1 and stage-2 preconditioner diagonals
+    // (h and 2h), for the float CG vector updates
+    hinv[i] = float(1.0 / hv);
+    hinv[M + i] = float(1.0 / (2.0 * hv));
 }
 
 __global__ void k_poisson_weights(int64_t count, const int64_t *dd, const int64_t *ii,
@@ -244,7 +249,8 @@ cudaError_t launch_plan_tables(Plan &p)
 cudaError_t launch_hess_diag(Plan &p)
 {
     k_hess_diag<<<blocks_for(p.M, 128), 128, 0, p.stream>>>(
-        p.M, p.gamma, p.lam, p.lo, p.hi, p.aoff, p.anchor, p.ratio_inv, p.adj_dlo, p.adj_dhi, p.h);
+        p.M, p.gamma, p.lam, p.lo, p.hi, p.aoff, p.anchor, p.ratio_inv, p.adj_dlo, p.adj_dhi, p.h,
+        p.hinv_f);
     count_launch();
     return cudaGetLastError();
 }

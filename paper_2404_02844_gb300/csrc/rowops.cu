@@ -24,6 +24,7 @@ struct RowArgs {
     int64_t M, N;
     double gamma;
     const double *h;     // Hessian diagonal (M)
+    const float *hinv;   // float 1/h (M) then 1/(2h) (M)
     double *partials;
     int64_t pstride;
     DevScalars *sc;
@@ -32,7 +33,7 @@ struct RowArgs {
 static RowArgs row_args(Plan &p)
 {
     RowArgs a;
-    a.M = p.M; a.N = p.N; a.gamma = p.gamma; a.h = p.h;
+    a.M = p.M; a.N = p.N; a.gamma = p.gamma; a.h = p.h; a.hinv = p.hinv_f;
     a.partials = p.partials; a.pstride = p.max_partials; a.sc = p.sc;
     return a;
 }
@@ -250,7 +251,7 @@ __global__ void k_setup2(RowArgs a, int stage, int max_cg, const double *Th, con
     const double eps = a.sc->eps;
     ROW_LOOP_BEGIN
     const double diag = stage == 1 ? a.h[i] : 2.0 * a.h[i];
-    const float inv = F32 ? float(1.0 / diag) : 0.f;
+    const float inv = F32 ? a.hinv[(stage == 1 ? 0 : a.M) + i] : 0.f;
     VT pv[VPL];
     VT psum = 0;
     float rz_row = 0.f, rr_row = 0.f;
@@ -380,9 +381,8 @@ __global__ void k_cg_update_xr(RowArgs a, int stage, const uint8_t *freem, const
     const double scale = stage == 1 ? 1.0 : 2.0;
     double rz = 0.0, rr = 0.0;
     ROW_LOOP_BEGIN
-    const double diag = scale * a.h[i];
     if constexpr (F32) {
-        const float inv = float(1.0 / diag);
+        const float inv = a.hinv[(stage == 1 ? 0 : a.M) + i];
         float rz_row = 0.f, rr_row = 0.f;
         for (int64_t n = lane; n < a.N; n += 32) {
             const int64_t e = i * a.N + n;
@@ -398,6 +398,7 @@ __global__ void k_cg_update_xr(RowArgs a, int stage, const uint8_t *freem, const
         rz += double(rz_row);
         rr += double(rr_row);
     } else {
+        const double diag = scale * a.h[i];
         for (int64_t n = lane; n < a.N; n += 32) {
             const int64_t e = i * a.N + n;
             const double xv = x[e] + al * p[e];

@@ -32,7 +32,8 @@
 namespace tomo {
 
 constexpr int TC_BK = 64;       // reduction slice per stage (one 128-byte bf16 row)
-constexpr int TC_STAGES = 2;
+constexpr int TC_STAGES = 2;      // A (weight) stages; the MMA barriers follow them
+constexpr int TC_BSTAGES = 3;     // B (vector) stages: B is copied one step ahead
 constexpr int TC_THREADS = 256;
 constexpr uint32_t TC_WAIT_LIMIT = 1u << 24;
 
@@ -41,15 +42,19 @@ struct TcLayout {
     static constexpr int NPART = SPLIT == 3 ? 2 : 1;                 // hi (+ lo)
     static constexpr int A_BYTES = TILE_R * TC_BK * 2;               // 16 KB
     static constexpr int B_BYTES = BN * TC_BK * 2;
-    static constexpr int STAGE_BYTES = NPART * (A_BYTES + B_BYTES);
+    static constexpr int A_STAGE = NPART * A_BYTES;
+    static constexpr int B_STAGE = NPART * B_BYTES;
+    static constexpr int STAGE_BYTES = TC_STAGES * A_STAGE + TC_BSTAGES * B_STAGE;  // all stages
     static constexpr int STAGING_BYTES = (TC_THREADS / 8) * 8 * 9 * 4;  // 8x8 transposes (+pad)
     static constexpr int CTRL_BYTES = 64;
     // per-unit tables: probe metadata (adjoint) and the 1/(i+1) pairs
     static constexpr int META_BYTES = TC_MAX_UNIT * 24;
     static constexpr int RINV_BYTES = (TC_MAX_UNIT + 2 * RUN + TILE_R) * 8;
-    static constexpr int TOTAL = 1024 + TC_STAGES * STAGE_BYTES + STAGING_BYTES + CTRL_BYTES +
+    static constexpr int TOTAL = 1024 + STAGE_BYTES + STAGING_BYTES + CTRL_BYTES +
                                  META_BYTES + RINV_BYTES;
     static constexpr int TMEM_COLS = BN < 32 ? 32 : BN;
+    static_assert(TOTAL <= 227 * 1024, "shared memory per CTA");
+    static_assert(TILE_R * (BN + 1) * 4 <= STAGE_BYTES, "epilogue tile fits the stage buffers");
 };
 
 struct TcArgs {
@@ -170,6 +175,14 @@ __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc)
 {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(tc::smem_u32(smem_dst)), "l"(gsrc) : "memory");
 }
+__device__ __forceinline__ void cp_async_commit()
+{
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_group1()
+{
+    asm volatile("cp.async.wait_group 1;" ::: "memory");
+}
 __device__ __forceinline__ void cp_async_wait_all()
 {
     asm volatile("cp.async.wait_all;" ::: "memory");
@@ -201,10 +214,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(TcArgs a)
     extern __shared__ unsigned char tc_raw[];
     const uint32_t raw_u32 = tc::smem_u32(tc_raw);
     unsigned char *sm = tc_raw + (((raw_u32 + 1023u) & ~1023u) - raw_u32);
-    float *staging = reinterpret_cast<float *>(sm + TC_STAGES * L::STAGE_BYTES);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + TC_STAGES * L::STAGE_BYTES + L::STAGING_BYTES);
+    float *staging = reinterpret_cast<float *>(sm + L::STAGE_BYTES);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + L::STAGE_BYTES + L::STAGING_BYTES);
     uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + TC_STAGES);
-    ProbeMeta *meta_s = reinterpret_cast<ProbeMeta *>(sm + TC_STAGES * L::STAGE_BYTES + L::STAGING_BYTES +
+    ProbeMeta *meta_s = reinterpret_cast<ProbeMeta *>(sm + L::STAGE_BYTES + L::STAGING_BYTES +
                                                       L::CTRL_BYTES);
     float2 *rinv_s = reinterpret_cast<float2 *>(reinterpret_cast<unsigned char *>(meta_s) + L::META_BYTES);
 
@@ -283,34 +296,46 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(TcArgs a)
         }
     }
 
-    for (int s = 0; s < nsteps; ++s) {
-        const uint32_t g = gstep + uint32_t(s);
-        const int st = int(g % TC_STAGES);
-        unsigned char *stage = sm + st * L::STAGE_BYTES;
-        unsigned char *A_hi = stage;
-        unsigned char *A_lo = stage + L::A_BYTES;                       // SPLIT == 3 only
-        unsigned char *B_hi = stage + L::NPART * L::A_BYTES;
-        unsigned char *B_lo = B_hi + L::B_BYTES;                        // SPLIT == 3 only
-        if (g >= TC_STAGES) {
-            // the MMAs issued TC_STAGES steps ago (maybe by the previous unit)
-            // read this stage
-            if (!tc::mbar_wait_bounded(&bars[st], ((g / TC_STAGES) - 1) & 1u, TC_WAIT_LIMIT))
-                ok = false;
-        }
-        const int64_t k0 = int64_t(wu.k0) + int64_t(s) * TC_BK;
-
-        // ---- operand B: transposed bf16 copy of the vector (asynchronous) ----
-        constexpr int BCH = BN * (TC_BK / 8);          // 16-byte chunks per part
+    // operand B of one step: the transposed bf16 copy of the vector, 16-byte
+    // asynchronous copies into B stage `bs`, as one copy group
+    constexpr int BCH = BN * (TC_BK / 8);          // 16-byte chunks per part
+    auto issue_b = [&](int64_t kb0, int bs) {
+        unsigned char *B_hi = sm + TC_STAGES * L::A_STAGE + bs * L::B_STAGE;
+        unsigned char *B_lo = B_hi + L::B_BYTES;
 #pragma unroll
         for (int q = 0; q < (L::NPART * BCH + TC_THREADS - 1) / TC_THREADS; ++q) {
             const int c = tid + q * TC_THREADS;
             if (c < L::NPART * BCH) {
                 const int part = c / BCH, cc = c % BCH;
                 const int n = cc / (TC_BK / 8), j = cc % (TC_BK / 8);
-                const __nv_bfloat16 *src = (part == 0 ? a.b_hi : a.b_lo) + (n0 + n) * a.bpitch + k0 + j * 8;
+                const __nv_bfloat16 *src = (part == 0 ? a.b_hi : a.b_lo) + (n0 + n) * a.bpitch + kb0 + j * 8;
                 cp_async16((part == 0 ? B_hi : B_lo) + tc::sw128_chunk(n, j), src);
             }
         }
+        cp_async_commit();
+    };
+
+    for (int s = 0; s < nsteps; ++s) {
+        const uint32_t g = gstep + uint32_t(s);
+        const int st = int(g % TC_STAGES);            // A stage and MMA barrier
+        const int bst = int(g % TC_BSTAGES);          // B stage
+        unsigned char *A_hi = sm + st * L::A_STAGE;
+        unsigned char *A_lo = A_hi + L::A_BYTES;                        // SPLIT == 3 only
+        unsigned char *B_hi = sm + TC_STAGES * L::A_STAGE + bst * L::B_STAGE;
+        unsigned char *B_lo = B_hi + L::B_BYTES;                        // SPLIT == 3 only
+        if (g >= TC_STAGES) {
+            // the MMAs of step g - 2 (maybe of the previous unit) read this A
+            // stage and the B stage of step g + 1; their completion also
+            // covers every earlier step
+            if (!tc::mbar_wait_bounded(&bars[st], ((g / TC_STAGES) - 1) & 1u, TC_WAIT_LIMIT))
+                ok = false;
+        }
+        const int64_t k0 = int64_t(wu.k0) + int64_t(s) * TC_BK;
+
+        // ---- operand B: this step's copy (first step of a unit) and the
+        // next step's, so that a copy's latency overlaps a whole step ----
+        if (s == 0) issue_b(k0, bst);
+        if (s + 1 < nsteps) issue_b(k0 + TC_BK, int((g + 1) % TC_BSTAGES));
         // ---- operand A: Poisson weights ----
         float anc_cur[QRUNS];
 #pragma unroll
@@ -351,7 +376,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(TcArgs a)
             *reinterpret_cast<uint4 *>(A_hi + tc::sw128_chunk(row, chunk)) = hi;
             if (SPLIT == 3) *reinterpret_cast<uint4 *>(A_lo + tc::sw128_chunk(row, chunk)) = lo;
         }
-        cp_async_wait_all();
+        // this step's B copy is complete when at most the next step's group
+        // is still in flight
+        if (s + 1 < nsteps) cp_async_wait_group1();
+        else cp_async_wait_all();
         tc::fence_proxy_async_smem();
         tc::tc_fence_before_sync();
         __syncthreads();
@@ -380,9 +408,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(TcArgs a)
     gstep += uint32_t(nsteps);
     tc::tc_fence_after_sync();
 
-    // ---- epilogue: tensor memory -> registers ----
-    // warp w reads TMEM lanes 32 (w % 4) .. + 31 (tile rows) and the column
-    // half w / 4 (BN >= 64) or all columns (BN == 32, warps 0-3 only)
+    // ---- epilogue, through a shared-memory copy of the tile ----
+    // (the stage buffers: every MMA and copy of this unit is complete).  Warp
+    // w reads TMEM lanes 32 (w % 4) .. + 31 (tile rows) and the column half
+    // w / 4 (BN >= 64) or all columns (BN == 32, warps 0-3 only); every
+    // global access below runs along rows (split-K partials, the adjoint's
+    // u and q) or along the transposed rows (the forward's O^T copies).
     const int lg = warp & 3;
     const int row = lg * 32 + lane;
     constexpr int COLS_PER_WARP = BN >= 64 ? BN / 2 : BN;
@@ -390,9 +421,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(TcArgs a)
     const bool active = BN >= 64 || warp < 4;
     const int nsplit = a.tile_nsplit[tile];
     const int ncb = gridDim.y;
-    const int64_t tile_elems = int64_t(TILE_R) * BN;
+    constexpr int LD = BN + 1;                 // padded row: conflict-free both ways
+    constexpr int TE = TILE_R * BN;
+    float *tile_s = reinterpret_cast<float *>(sm);
 
-    float acc[COLS_PER_WARP];
     if (active) {
 #pragma unroll
         for (int c = 0; c < COLS_PER_WARP; c += 32) {
@@ -404,18 +436,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(TcArgs a)
                 for (int k = 0; k < 32; ++k) r[k] = 0u;
             }
 #pragma unroll
-            for (int k = 0; k < 32; ++k) acc[c + k] = __uint_as_float(r[k]);
+            for (int k = 0; k < 32; ++k) tile_s[row * LD + col0 + c + k] = __uint_as_float(r[k]);
         }
     }
+    __syncthreads();
     bool owner = true;
     if (nsplit > 1) {
-        float *mine = a.part + (int64_t(a.tile_first[tile] + wu.chunk) * ncb + blockIdx.y) * tile_elems;
-        if (active) {
-#pragma unroll
-            for (int c = 0; c < COLS_PER_WARP; c += 4)
-                *reinterpret_cast<float4 *>(&mine[row * BN + col0 + c]) =
-                    make_float4(acc[c], acc[c + 1], acc[c + 2], acc[c + 3]);
-        }
+        // this unit's partial tile, then the split-K ticket: the unit that
+        // completes the tile sums every partial in unit order (deterministic)
+        const int64_t split_stride = int64_t(ncb) * TE;
+        const float *base = a.part + (int64_t(a.tile_first[tile]) * ncb + blockIdx.y) * TE;
+        float *mine = a.part + (int64_t(a.tile_first[tile] + wu.chunk) * ncb + blockIdx.y) * TE;
+        for (int e = tid; e < TE; e += TC_THREADS) mine[e] = tile_s[(e / BN) * LD + (e % BN)];
         __threadfence();
         __syncthreads();
         if (tid == 0) {
@@ -425,51 +457,52 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(TcArgs a)
         }
         __syncthreads();
         owner = last != 0;
-        if (owner && active) {
+        if (owner) {
             __threadfence();
+            // each thread sums P4 float4 columns of the tile over the splits,
+            // split by split (P4 independent loads in flight per thread)
+            constexpr int P4 = TE / 4 / TC_THREADS;
+            static_assert(TE % (4 * TC_THREADS) == 0, "tile divides into float4 per thread");
+            float4 acc4[P4];
 #pragma unroll
-            for (int c = 0; c < COLS_PER_WARP; ++c) acc[c] = 0.f;
+            for (int j = 0; j < P4; ++j) acc4[j] = make_float4(0.f, 0.f, 0.f, 0.f);
             for (int sidx = 0; sidx < nsplit; ++sidx) {
-                const float *src = a.part + (int64_t(a.tile_first[tile] + sidx) * ncb + blockIdx.y) * tile_elems;
+                const float4 *src = reinterpret_cast<const float4 *>(base + sidx * split_stride);
+                float4 t[P4];
 #pragma unroll
-                for (int c = 0; c < COLS_PER_WARP; c += 4) {
-                    const float4 t = __ldcg(reinterpret_cast<const float4 *>(&src[row * BN + col0 + c]));
-                    acc[c] += t.x; acc[c + 1] += t.y; acc[c + 2] += t.z; acc[c + 3] += t.w;
+                for (int j = 0; j < P4; ++j) t[j] = __ldcg(src + tid + j * TC_THREADS);
+#pragma unroll
+                for (int j = 0; j < P4; ++j) {
+                    acc4[j].x += t[j].x; acc4[j].y += t[j].y; acc4[j].z += t[j].z; acc4[j].w += t[j].w;
                 }
             }
+#pragma unroll
+            for (int j = 0; j < P4; ++j) {
+                const int e = (tid + j * TC_THREADS) * 4, rr = e / BN, cc = e % BN;
+                float *d = &tile_s[rr * LD + cc];
+                d[0] = acc4[j].x; d[1] = acc4[j].y; d[2] = acc4[j].z; d[3] = acc4[j].w;
+            }
+            __syncthreads();
         }
     }
-    if (owner && active) {
-        const int64_t grow = r0 + row;
-        if (FWD) {
-            // O^T hi/lo copies for the adjoint's operand B
-            if (grow < a.D) {
-#pragma unroll
-                for (int c = 0; c < COLS_PER_WARP; ++c) {
-                    const int64_t n = n0 + col0 + c;
-                    if (n < a.N) {
-                        const __nv_bfloat16 h = __float2bfloat16_rn(acc[c]);
-                        a.o_hi[n * a.opitch + grow] = h;
-                        a.o_lo[n * a.opitch + grow] = __float2bfloat16_rn(acc[c] - __bfloat162float(h));
-                    }
-                }
-            }
+    if (FWD && owner) {
+        // O^T hi/lo copies for the adjoint's operand B: consecutive threads
+        // take consecutive probes of one outcome column
+        for (int e = tid; e < TE; e += TC_THREADS) {
+            const int nl = e / TILE_R, rr = e % TILE_R;
+            const int64_t grow = r0 + rr, n = n0 + nl;
+            if (grow >= a.D || n >= a.N) continue;
+            const float v = tile_s[rr * LD + nl];
+            const __nv_bfloat16 h = __float2bfloat16_rn(v);
+            a.o_hi[n * a.opitch + grow] = h;
+            a.o_lo[n * a.opitch + grow] = __float2bfloat16_rn(v - __bfloat162float(h));
         }
     }
     if (!FWD && owner) {
-        // q = 2 Z + 2 gamma L u through a shared-memory copy of the tile (the
-        // stage buffers: this unit's MMAs and copies are complete), so that
-        // the reads of u and the writes of q run along rows (coalesced)
-        constexpr int LD = BN + 1;
-        float *tile_s = reinterpret_cast<float *>(sm);
-        if (active) {
-#pragma unroll
-            for (int c = 0; c < COLS_PER_WARP; ++c) tile_s[row * LD + col0 + c] = acc[c];
-        }
-        __syncthreads();
+        // q = 2 Z + 2 gamma L u along rows
         const double g2 = 2.0 * a.gamma;
         const float g2f = float(g2);
-        for (int e = tid; e < TILE_R * BN; e += TC_THREADS) {
+        for (int e = tid; e < TE; e += TC_THREADS) {
             const int rr = e / BN, cc = e - (e / BN) * BN;
             const int64_t grow = r0 + rr, n = n0 + cc;
             if (grow >= a.M || n >= a.N) continue;

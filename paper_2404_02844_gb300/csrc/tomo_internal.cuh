@@ -87,6 +87,7 @@ struct Plan {
     int32_t *fwd_klo, *fwd_khi;  // per forward tile (probes)
     int32_t *adj_dlo, *adj_dhi;  // per adjoint tile (photon numbers)
     double *h;         // M: Hessian diagonal
+    float *hinv_f;     // 2 M: float 1/h and 1/(2h) (stage-1 and stage-2 preconditioners)
     int64_t n_anchor;
     int fwd_tiles, adj_tiles;
     Schedule sched[2][2];      // [forward, adjoint][float, double]

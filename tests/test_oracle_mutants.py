@@ -154,10 +154,12 @@ def checks(L):
             failed.append("solve")
         if not (abs(oracle.poisson(7, 3.5) - poisson.pmf(7, 3.5)) <= 1e-13 * poisson.pmf(7, 3.5)):
             failed.append("poisson")
-        # Armijo (App. B): every accepted step decreases f (c1, first iterations)
+        # Armijo (App. B): every accepted step decreases f (c1, first 30
+        # iterations; CG capped at 50 products so that full steps overshoot
+        # and the rule has to reject some trials)
         w = workloads.config_c1()
         pc = oracle.Problem.from_workload(w)
-        _, _, hc = pc.fit(w.P, max_newton=20, eps_kkt=0.0)
+        _, _, hc = pc.fit(w.P, max_newton=30, eps_kkt=0.0, max_cg=50)
         if not np.all(np.diff(hc) <= 0.0):
             failed.append("monotone")
     finally:
