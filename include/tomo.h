@@ -237,6 +237,59 @@ tomo_status tomo_poisson_weights(tomo_plan_t plan, const int64_t *d, const int64
 /* Band bounds lo_d, hi_d as computed by the plan (HOST arrays of D). */
 tomo_status tomo_bands(tomo_plan_t plan, int64_t *lo_host, int64_t *hi_host);
 
+/* ---- learned warm start ----------------------------------------------------
+ * The paper has no counterpart: it starts Algorithm 3 from Theta^(0) = 1/N.
+ * A small network maps measured frequencies P (D probes x C0 outcome columns,
+ * the columns n >= ncols of a sample zero) to a starting POVM Theta0 (M x C0,
+ * each row a softmax over its first ncols columns, hence on the simplex):
+ *   Y1 = conv1d(P, W1, b1, stride S1)        (D/S1) x C1
+ *   Y2 = conv1d(relu(Y1), W2, b2, stride S2) (D/S1/S2) x C2
+ *   Y3 = W3 flat(relu(Y2)) + b3              H
+ *   Z  = W4 relu(Y3) + b4                    M x C0 logits
+ * conv1d(X, W, b, S)[t, co] = b[co] + sum_{ci,k} W[co,ci,k] X[S t + k - K/2, ci]
+ * (zero padding).  Training minimises the row-wise cross-entropy against
+ * target POVMs (mean over rows and samples) with Adam (beta1 0.9, beta2
+ * 0.999, eps 1e-8); float arithmetic and float master weights; inference
+ * reads a bf16 copy of the weights with float accumulation.  Parameters form
+ * one float vector: W1 (C1 x C0 x K), b1, W2 (C2 x C1 x K), b2, W3 (H x F,
+ * F = D/S1/S2 * C2, flattened t-major), b3, W4 (M C0 x H), b4 (M C0). */
+typedef struct tomo_ws_s *tomo_ws_t;
+
+typedef struct {
+    int64_t D, C0, M;       /* probes, padded outcome columns (2..256), photon numbers */
+    int64_t C1, C2, K;      /* conv channels and kernel width */
+    int64_t S1, S2, H;      /* conv strides (D % S1 == 0, (D/S1) % S2 == 0), hidden width */
+    int64_t max_batch;      /* largest training batch */
+    uint64_t seed;          /* SplitMix64 seed of the He-uniform initialisation */
+    void *stream;           /* cudaStream_t; NULL: the handle owns a stream */
+} tomo_ws_desc;
+
+/* Allocates the parameters, Adam state and activations (device) and
+ * initialises the weights.  EINVAL on a shape out of range. */
+tomo_status tomo_ws_create(tomo_ws_t *out, const tomo_ws_desc *desc);
+void tomo_ws_destroy(tomo_ws_t ws);
+/* Number of parameters (-1 for a NULL handle). */
+int64_t tomo_ws_param_count(tomo_ws_t ws);
+/* Copy the float parameters to / from HOST memory (set also resets Adam). */
+tomo_status tomo_ws_get_params(tomo_ws_t ws, float *host);
+tomo_status tomo_ws_set_params(tomo_ws_t ws, const float *host);
+/* Mean cross-entropy of a batch and its gradient (no update).  P: B x D x C0,
+ * T: B x M x C0 doubles in device memory (padded columns ignored); ncols:
+ * HOST array of B column counts (1..C0); grad_host (nullable) receives
+ * tomo_ws_param_count floats. */
+tomo_status tomo_ws_loss_grad(tomo_ws_t ws, const double *P, const double *T, const int32_t *ncols,
+                              int32_t B, float *loss_host, float *grad_host);
+/* One Adam step on the batch (same inputs); loss_host (nullable) receives
+ * the batch loss before the step. */
+tomo_status tomo_ws_train_step(tomo_ws_t ws, const double *P, const double *T, const int32_t *ncols,
+                               int32_t B, float lr, float *loss_host);
+/* Theta0 (M x N doubles, device) for one problem's P (D x N doubles, device,
+ * N <= C0 columns, unpadded): every row on the simplex. */
+tomo_status tomo_ws_infer(tomo_ws_t ws, const double *P, int64_t N, double *Theta0);
+/* Parameter file: magic "TOMOWS01", the nine shape fields, the floats. */
+tomo_status tomo_ws_save(tomo_ws_t ws, const char *path);
+tomo_status tomo_ws_load(tomo_ws_t ws, const char *path);
+
 /* Kernel launches made by this library since it was loaded (all threads,
  * all entry points), for launch accounting. */
 int64_t tomo_kernel_launches(void);

@@ -22,7 +22,7 @@ __all__ = ["Plan", "TomoError", "lib", "tomo_plan", "tomo_plan_destroy", "tomo_o
            "tomo_fit", "tomo_fit_opts_default", "tomo_apply_F", "tomo_apply_Ft", "tomo_hvp",
            "tomo_hess_diag", "tomo_project_simplex", "tomo_kkt", "tomo_poisson_weights",
            "tomo_bands", "tomo_kernel_launches", "tomo_last_error", "PREC_FP64", "PREC_FP32",
-           "STATUS", "STOP"]
+           "STATUS", "STOP", "WarmStart", "fit_warm", "tomo_smooth"]
 
 PREC_FP64 = 0
 PREC_FP32 = 1
@@ -58,6 +58,12 @@ class tomo_fit_report(ctypes.Structure):
                 ("fwd_ms", c_dbl), ("adj_ms", c_dbl)]
 
 
+class tomo_ws_desc(ctypes.Structure):
+    _fields_ = [("D", c_i64), ("C0", c_i64), ("M", c_i64), ("C1", c_i64), ("C2", c_i64),
+                ("K", c_i64), ("S1", c_i64), ("S2", c_i64), ("H", c_i64), ("max_batch", c_i64),
+                ("seed", ctypes.c_uint64), ("stream", c_ptr)]
+
+
 # (name, restype, argtypes) of every entry point of include/tomo.h
 EXPORTS = [
     ("tomo_plan", c_i32, [ctypes.POINTER(c_ptr), ctypes.POINTER(tomo_desc)]),
@@ -80,6 +86,17 @@ EXPORTS = [
     ("tomo_bands", c_i32, [c_ptr, c_ptr, c_ptr]),
     ("tomo_objective_noalloc", c_i32, [c_i64, c_i64, c_i64, c_ptr, c_dbl, c_dbl, c_ptr, c_ptr,
                                        c_ptr, c_ptr]),
+    ("tomo_ws_create", c_i32, [ctypes.POINTER(c_ptr), ctypes.POINTER(tomo_ws_desc)]),
+    ("tomo_ws_destroy", None, [c_ptr]),
+    ("tomo_ws_param_count", c_i64, [c_ptr]),
+    ("tomo_ws_get_params", c_i32, [c_ptr, c_ptr]),
+    ("tomo_ws_set_params", c_i32, [c_ptr, c_ptr]),
+    ("tomo_ws_loss_grad", c_i32, [c_ptr, c_ptr, c_ptr, c_ptr, c_i32, ctypes.POINTER(ctypes.c_float), c_ptr]),
+    ("tomo_ws_train_step", c_i32, [c_ptr, c_ptr, c_ptr, c_ptr, c_i32, ctypes.c_float,
+                                   ctypes.POINTER(ctypes.c_float)]),
+    ("tomo_ws_infer", c_i32, [c_ptr, c_ptr, c_i64, c_ptr]),
+    ("tomo_ws_save", c_i32, [c_ptr, ctypes.c_char_p]),
+    ("tomo_ws_load", c_i32, [c_ptr, ctypes.c_char_p]),
     ("tomo_kernel_launches", c_i64, []),
     ("tomo_last_error", ctypes.c_char_p, []),
 ]
@@ -392,3 +409,106 @@ class Plan:
         hi = np.empty(self.D, np.int64)
         tomo_bands(self._h, lo.ctypes.data, hi.ctypes.data)
         return lo, hi
+
+
+# ---------------------------------------------------------------------------
+# learned warm start
+# ---------------------------------------------------------------------------
+class WarmStart:
+    """Handle of the learned warm start (tomo_ws_*): a conv1d encoder over the
+    probes, an MLP and a per-row softmax giving a feasible Theta0.  Batches
+    are float64 torch CUDA tensors: P (B, D, C0) and targets (B, M, C0),
+    padded with zero columns beyond each sample's ncols."""
+
+    def __init__(self, D, C0, M, C1=32, C2=32, K=5, S1=2, S2=4, H=32, max_batch=32, seed=1,
+                 stream=None):
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        d = tomo_ws_desc(D, C0, M, C1, C2, K, S1, S2, H, max_batch, seed, c_ptr(stream))
+        h = c_ptr()
+        _check(lib().tomo_ws_create(ctypes.byref(h), ctypes.byref(d)), "tomo_ws_create")
+        self._h = h.value
+        self.shape = dict(D=D, C0=C0, M=M, C1=C1, C2=C2, K=K, S1=S1, S2=S2, H=H)
+        self.max_batch = max_batch
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().tomo_ws_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def param_count(self) -> int:
+        return int(lib().tomo_ws_param_count(self._h))
+
+    def params(self) -> np.ndarray:
+        out = np.empty(self.param_count, dtype=np.float32)
+        _check(lib().tomo_ws_get_params(self._h, out.ctypes.data), "tomo_ws_get_params")
+        return out
+
+    def set_params(self, values) -> None:
+        v = np.ascontiguousarray(values, dtype=np.float32)
+        if v.size != self.param_count:
+            raise ValueError("parameter vector of the wrong length")
+        _check(lib().tomo_ws_set_params(self._h, v.ctypes.data), "tomo_ws_set_params")
+
+    @staticmethod
+    def _ncols(ncols):
+        return np.ascontiguousarray(ncols, dtype=np.int32)
+
+    def loss_grad(self, P, T, ncols):
+        nc = self._ncols(ncols)
+        loss = ctypes.c_float()
+        g = np.empty(self.param_count, dtype=np.float32)
+        _check(lib().tomo_ws_loss_grad(self._h, _ptr(P), _ptr(T), nc.ctypes.data, int(nc.size),
+                                       ctypes.byref(loss), g.ctypes.data), "tomo_ws_loss_grad")
+        return float(loss.value), g
+
+    def train_step(self, P, T, ncols, lr=1e-3) -> float:
+        nc = self._ncols(ncols)
+        loss = ctypes.c_float()
+        _check(lib().tomo_ws_train_step(self._h, _ptr(P), _ptr(T), nc.ctypes.data, int(nc.size),
+                                        float(lr), ctypes.byref(loss)), "tomo_ws_train_step")
+        return float(loss.value)
+
+    def infer(self, P):
+        """Theta0 (M x N) for one problem's P (D x N, float64 CUDA tensor)."""
+        import torch
+        N = int(P.shape[1])
+        out = torch.empty(self.shape["M"], N, dtype=torch.float64, device="cuda")
+        _check(lib().tomo_ws_infer(self._h, _ptr(P), N, _ptr(out)), "tomo_ws_infer")
+        return out
+
+    def save(self, path) -> None:
+        _check(lib().tomo_ws_save(self._h, str(path).encode()), "tomo_ws_save")
+
+    def load(self, path) -> None:
+        _check(lib().tomo_ws_load(self._h, str(path).encode()), "tomo_ws_load")
+
+
+def fit_warm(plan, ws, P, **opts):
+    """Algorithm 3 started from the learned Theta0, falling back to 1/N when
+    f(Theta0) >= f(1/N) or when the warm-started fit fails.  Returns (Theta,
+    report, used_warm_start)."""
+    import torch
+    Th0 = ws.infer(P)
+    uni = torch.full_like(Th0, 1.0 / Th0.shape[1])
+    use = plan.objective(P, Th0) < plan.objective(P, uni)
+    if use:
+        Th, rep = plan.fit(P, Th0, **opts)
+        if rep["status"] in ("TOMO_OK", "TOMO_ENOTCONV") and np.isfinite(rep["f"]):
+            return Th, rep, True
+    Th, rep = plan.fit(P, **opts)
+    return Th, rep, False

@@ -19,7 +19,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libtomo.so")
 INCLUDE = os.path.join(ROOT, "include")
 
-SOURCES = ["plan.cu", "band_gemm.cu", "tc_band.cu", "rowops.cu", "smooth.cu", "api.cu", "noalloc.cu"]
+SOURCES = ["plan.cu", "band_gemm.cu", "tc_band.cu", "rowops.cu", "smooth.cu", "warmstart.cu", "api.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
               "--expt-relaxed-constexpr", "-Xptxas", "-O3"]

@@ -243,3 +243,57 @@ def random_feasible_theta(M: int, N: int, rng: np.random.Generator,
     x[rng.random((M, N)) < sparsity] = 0.0
     x[np.arange(M), rng.integers(0, N, M)] += 0.5
     return x / x.sum(axis=1, keepdims=True)
+
+
+# ---- learned warm start: detector population -------------------------------
+C5_M, C5_D, C5_X, C5_C0, C5_GAMMA, C5_SHOTS = 1024, 2048, 768.0, 64, 1e-3, 1_000_000
+
+
+def dense_poisson(M: int, lam: np.ndarray) -> np.ndarray:
+    """F_{d,i} = Poisson(i; lambda_d) for i < M from scipy's pmf (dense)."""
+    from scipy.stats import poisson
+    return poisson.pmf(np.arange(M)[None, :], np.asarray(lam)[:, None])
+
+
+def config_c5_instance(j: int, F: np.ndarray | None = None, M: int = C5_M, D: int = C5_D,
+                       X: float = C5_X, shots=C5_SHOTS, bins_range=(16, 63),
+                       gamma: float = C5_GAMMA) -> Workload:
+    """Instance j of the warm-start detector population: bins ~ U{16..63}
+    (N = bins + 1 <= 64), efficiency U[0.3, 0.95], crosstalk U[0, 1e-2], dark
+    counts U[0, 1e-3] per bin; D probes with lambda linear in [0, X]; dense
+    outcome probabilities q = F Theta_true, multinomial shots.  Seed
+    BASE_SEED + 4 + 1000 j.  F (D x M, from dense_poisson) may be passed in to
+    share it across instances."""
+    seed = BASE_SEED + 4 + 1000 * j
+    rng = np.random.Generator(np.random.PCG64(seed))
+    bins = int(rng.integers(bins_range[0], bins_range[1] + 1))
+    eta = float(rng.uniform(0.3, 0.95))
+    xt = float(rng.uniform(0.0, 1e-2))
+    dark = float(rng.uniform(0.0, 1e-3))
+    lam = probe_intensities(D, X)
+    if F is None:
+        F = dense_poisson(M, lam)
+    theta = detector_povm(M, bins, eta, p_dark=dark, crosstalk=xt)
+    q = F @ theta
+    if shots is None:
+        P = q
+    else:
+        p = np.maximum(q, 0.0)
+        p /= p.sum(axis=1, keepdims=True)
+        P = rng.multinomial(int(shots), p) / float(shots)
+    return Workload(f"c5_{j}_N{bins + 1}", M, bins + 1, D, lam, P, theta, gamma, 10.0, seed, shots)
+
+
+def c5_batch(js, F=None, C0: int = C5_C0, **kw):
+    """Padded arrays of instances js: P (B, D, C0), Theta_true (B, M, C0),
+    ncols (B,)."""
+    ws = [config_c5_instance(j, F=F, **kw) for j in js]
+    B, D, M = len(ws), ws[0].D, ws[0].M
+    P = np.zeros((B, D, C0))
+    T = np.zeros((B, M, C0))
+    nc = np.zeros(B, dtype=np.int32)
+    for b, w in enumerate(ws):
+        P[b, :, :w.N] = w.P
+        T[b, :, :w.N] = w.theta_true
+        nc[b] = w.N
+    return P, T, nc, ws
