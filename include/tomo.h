@@ -76,6 +76,14 @@ typedef enum {
 
 typedef struct tomo_plan_s *tomo_plan_t;
 
+/* tomo_desc.flags: time candidate schedule densities of the CG Hessian
+ * product at plan time and keep the fastest (SIMT forms: work units per SM
+ * and column block in {1, 2, 4, 8}; tensor-core form: persistent CTAs per
+ * column block in {all SMs, 3/4, 1/2}).  Choices are cached per process by
+ * (precision form, N, power-of-two class of M and of D), so a batch of
+ * instances of one class tunes once.  The paper has no counterpart. */
+#define TOMO_PLAN_AUTOTUNE 1u
+
 /* Problem descriptor (Eq. min, Eq. Fmatrix, Eq. regul). */
 typedef struct {
     int64_t M;             /* photon-number cutoff: i = 0..M-1, 1 <= M <= 2^30 */
@@ -94,7 +102,7 @@ typedef struct {
     int32_t reserved;
     void *stream;          /* cudaStream_t to order work on; NULL: the plan
                               creates and owns a non-blocking stream */
-    uint32_t flags;        /* must be 0 */
+    uint32_t flags;        /* 0 or TOMO_PLAN_AUTOTUNE */
 } tomo_desc;
 
 /* Builds a plan: validates the descriptor, computes the probe bands, the
@@ -202,6 +210,19 @@ tomo_status tomo_apply_Ft(tomo_plan_t plan, const double *Y, double *Z);
 /* Hessian product (Table ops): HV = 2 F^T F V + 2 gamma L V, M x N, in the
  * arithmetic of the plan's CG products (tensor cores for TC plans). */
 tomo_status tomo_hvp(tomo_plan_t plan, const double *V, double *HV);
+
+/* Schedule chosen for the plan's CG Hessian product. */
+typedef struct {
+    int32_t autotuned;      /* 1 if TOMO_PLAN_AUTOTUNE chose the density */
+    int32_t from_cache;     /* 1 if the choice came from the per-process cache */
+    int32_t tensor_cores;   /* 1 for the tensor-core form */
+    int32_t density;        /* SIMT units per SM, or tensor-core CTAs per column block */
+    double hvp_ms;          /* timed Hessian product of the chosen density (0 if not tuned) */
+    int32_t units_fwd, units_adj;   /* work units of the forward / adjoint contraction */
+    int32_t ctas_fwd, ctas_adj;     /* CTAs launched per column block */
+} tomo_plan_info_t;
+
+tomo_status tomo_plan_info(tomo_plan_t plan, tomo_plan_info_t *info);
 
 /* Hessian diagonal h_i = 2 sum_d F_{d,i}^2 + 2 gamma L_ii (Table ops), M
  * doubles, always computed in double at plan time. */

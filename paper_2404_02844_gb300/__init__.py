@@ -58,6 +58,15 @@ class tomo_fit_report(ctypes.Structure):
                 ("fwd_ms", c_dbl), ("adj_ms", c_dbl)]
 
 
+PLAN_AUTOTUNE = 1
+
+
+class tomo_plan_info_t(ctypes.Structure):
+    _fields_ = [("autotuned", c_i32), ("from_cache", c_i32), ("tensor_cores", c_i32),
+                ("density", c_i32), ("hvp_ms", c_dbl), ("units_fwd", c_i32), ("units_adj", c_i32),
+                ("ctas_fwd", c_i32), ("ctas_adj", c_i32)]
+
+
 class tomo_ws_desc(ctypes.Structure):
     _fields_ = [("D", c_i64), ("C0", c_i64), ("M", c_i64), ("C1", c_i64), ("C2", c_i64),
                 ("K", c_i64), ("S1", c_i64), ("S2", c_i64), ("H", c_i64), ("max_batch", c_i64),
@@ -79,6 +88,7 @@ EXPORTS = [
     ("tomo_apply_Ft", c_i32, [c_ptr, c_ptr, c_ptr]),
     ("tomo_hvp", c_i32, [c_ptr, c_ptr, c_ptr]),
     ("tomo_hess_diag", c_i32, [c_ptr, c_ptr]),
+    ("tomo_plan_info", c_i32, [c_ptr, ctypes.POINTER(tomo_plan_info_t)]),
     ("tomo_project_simplex", c_i32, [c_ptr, c_ptr, c_ptr]),
     ("tomo_smooth", c_i32, [c_ptr, c_ptr, c_ptr, c_i64, c_dbl]),
     ("tomo_kkt", c_i32, [c_ptr, c_ptr, c_ptr, ctypes.POINTER(c_dbl)]),
@@ -177,10 +187,10 @@ def tomo_fit_batched(descs, P_ptrs, Theta_ptrs, opts=None, concurrency=8):
     return [int(x) for x in sts], [_fit_dict(r) for r in reps]
 
 
-def fit_batched(problems, precision="fp32", concurrency=8, **opts):
+def fit_batched(problems, precision="fp32", concurrency=8, autotune=False, **opts):
     """problems: list of (M, N, lam, band_k, gamma, P, Theta) with P, Theta
     float64 CUDA tensors (Theta receives the result).  Returns (statuses,
-    reports)."""
+    reports).  autotune: plan every instance with TOMO_PLAN_AUTOTUNE."""
     prec = {"fp64": PREC_FP64, "fp32": PREC_FP32, "mixed": PREC_MIXED, "tc": PREC_TC}[precision]
     o = tomo_fit_opts_default()
     for k, v in opts.items():
@@ -197,7 +207,7 @@ def fit_batched(problems, precision="fp32", concurrency=8, **opts):
         lam = np.ascontiguousarray(lam, dtype=np.float64)
         keep.append(lam)
         descs.append(tomo_desc(int(M), int(N), lam.shape[0], lam.ctypes.data, float(band_k),
-                               float(gamma), prec, 0, stream or None, 0))
+                               float(gamma), prec, 0, stream or None, PLAN_AUTOTUNE if autotune else 0))
         Pp.append(_ptr(P))
         Tp.append(_ptr(Theta))
     return tomo_fit_batched(descs, Pp, Tp, o, concurrency)
@@ -279,7 +289,8 @@ class Plan:
     Work is ordered on torch's current CUDA stream at construction unless a
     raw ``stream`` handle is given."""
 
-    def __init__(self, M, N, lam, band_k=10.0, gamma=0.0, precision="fp64", stream=None):
+    def __init__(self, M, N, lam, band_k=10.0, gamma=0.0, precision="fp64", stream=None,
+                 autotune=False):
         lam = np.ascontiguousarray(lam, dtype=np.float64)
         self.M, self.N, self.D = int(M), int(N), int(lam.shape[0])
         self.band_k, self.gamma = float(band_k), float(gamma)
@@ -294,8 +305,14 @@ class Plan:
                 stream = None
         self._lam = lam
         desc = tomo_desc(self.M, self.N, self.D, lam.ctypes.data, self.band_k, self.gamma,
-                         self.precision, 0, stream or None, 0)
+                         self.precision, 0, stream or None, PLAN_AUTOTUNE if autotune else 0)
         self._h = tomo_plan(desc)
+
+    def info(self) -> dict:
+        """The schedule of the CG Hessian product (tomo_plan_info)."""
+        i = tomo_plan_info_t()
+        _check(lib().tomo_plan_info(self._h, ctypes.byref(i)), "tomo_plan_info")
+        return {k: getattr(i, k) for k, _ in i._fields_}
 
     @classmethod
     def from_workload(cls, w, precision="fp64", **kw):

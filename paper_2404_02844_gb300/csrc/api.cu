@@ -17,6 +17,9 @@
 #include <thread>
 #include <utility>
 #include <vector>
+#include <tuple>
+#include <mutex>
+#include <map>
 
 #include "tomo_internal.cuh"
 
@@ -77,6 +80,14 @@ static cudaError_t dalloc(T **p, int64_t count)
     return cudaMalloc(reinterpret_cast<void **>(p), sizeof(T) * size_t(count));
 }
 
+static void free_schedule(Schedule &s)
+{
+    void *sd[] = {s.units, s.tile_first, s.tile_nsplit, s.counters, s.part, s.cta_first};
+    for (void *d : sd)
+        if (d) cudaFree(d);
+    s = Schedule{};
+}
+
 static void free_plan(Plan *p)
 {
     if (!p) return;
@@ -87,11 +98,7 @@ static void free_plan(Plan *p)
                    p->partials, p->sc, p->idx_buf, p->val_buf};
     for (void *d : dev)
         if (d) cudaFree(d);
-    auto free_sched = [](Schedule &s) {
-        void *sd[] = {s.units, s.tile_first, s.tile_nsplit, s.counters, s.part, s.cta_first};
-        for (void *d : sd)
-            if (d) cudaFree(d);
-    };
+    auto free_sched = [](Schedule &s) { free_schedule(s); };
     for (auto &row : p->sched)
         for (Schedule &s : row) free_sched(s);
     for (Schedule &s : p->sched_tc) free_sched(s);
@@ -309,7 +316,8 @@ static cudaError_t build_schedules(Plan &p, bool tensor_cores)
             // forward: K steps aligned to BK from 0; adjoint: probe ranges as they are
             ranges(fwd, fwd ? BK : 1, fwd ? BK : 1, st, en);
             if ((e = make_schedule(p, p.sched[dir][dbl], st, en, BK,
-                                   dbl ? sizeof(double) : sizeof(float), &max_ctas)))
+                                   dbl ? sizeof(double) : sizeof(float), &max_ctas, INT64_MAX,
+                                   p.ups_simt > 0 ? p.ups_simt : 4)))
                 return e;
         }
     }
@@ -322,24 +330,142 @@ static cudaError_t build_schedules(Plan &p, bool tensor_cores)
             // one CTA per SM (shared memory): one wave of persistent CTAs
             // with equal shares of the reduction work
             const int64_t ncol = (p.N + band_bn(p.N) - 1) / band_bn(p.N);
+            const int64_t ctas = p.tc_ctas > 0 ? std::min<int64_t>(p.tc_ctas, p.num_sms / ncol)
+                                               : p.num_sms / ncol;
             if ((e = make_schedule_tc(p, p.sched_tc[dir], st, en, 64, TC_MAX_UNIT,
-                                      std::max<int64_t>(1, p.num_sms / ncol), &max_ctas)))
+                                      std::max<int64_t>(1, ctas), &max_ctas)))
                 return e;
         }
-        const int64_t npad = ((p.N + 127) / 128) * 128;
-        p.ut_pitch = ((p.M + 63) / 64) * 64;
-        p.ot_pitch = ((p.D + 63) / 64) * 64;
-        const size_t ub = sizeof(__nv_bfloat16) * size_t(npad * p.ut_pitch);
-        const size_t ob = sizeof(__nv_bfloat16) * size_t(npad * p.ot_pitch);
-        if ((e = cudaMalloc(&p.ut_hi, ub)) || (e = cudaMalloc(&p.ut_lo, ub)) ||
-            (e = cudaMalloc(&p.ot_hi, ob)) || (e = cudaMalloc(&p.ot_lo, ob)))
-            return e;
-        if ((e = cudaMemset(p.ut_hi, 0, ub)) || (e = cudaMemset(p.ut_lo, 0, ub)) ||
-            (e = cudaMemset(p.ot_hi, 0, ob)) || (e = cudaMemset(p.ot_lo, 0, ob)))
-            return e;
+        if (!p.ut_hi) {  // transposed operand mirrors (kept across schedule rebuilds)
+            const int64_t npad = ((p.N + 127) / 128) * 128;
+            p.ut_pitch = ((p.M + 63) / 64) * 64;
+            p.ot_pitch = ((p.D + 63) / 64) * 64;
+            const size_t ub = sizeof(__nv_bfloat16) * size_t(npad * p.ut_pitch);
+            const size_t ob = sizeof(__nv_bfloat16) * size_t(npad * p.ot_pitch);
+            if ((e = cudaMalloc(&p.ut_hi, ub)) || (e = cudaMalloc(&p.ut_lo, ub)) ||
+                (e = cudaMalloc(&p.ot_hi, ob)) || (e = cudaMalloc(&p.ot_lo, ob)))
+                return e;
+            if ((e = cudaMemset(p.ut_hi, 0, ub)) || (e = cudaMemset(p.ut_lo, 0, ub)) ||
+                (e = cudaMemset(p.ot_hi, 0, ob)) || (e = cudaMemset(p.ot_lo, 0, ob)))
+                return e;
+        }
     }
     p.max_partials = std::max<int64_t>(p.max_partials, max_ctas);
     return cudaSuccess;
+}
+
+// ---------------------------------------------------------------------------
+// Plan-time autotuner of the schedule density.  Candidates: SIMT units per SM
+// and column block {1, 2, 4, 8}, or tensor-core persistent CTAs per column
+// block {all SMs, 3/4, 1/2}.  Each candidate's schedules are built and the
+// Hessian product is timed (CUDA events on the plan stream, best of 3 after
+// one warm-up); the fastest is kept.  Choices are cached per process by
+// (form, N, power-of-two class of M, of D), so instances of one class in a
+// batch tune once.
+// ---------------------------------------------------------------------------
+struct TuneKey {
+    int prec;
+    int64_t N;
+    int lm, ld;
+    bool operator<(const TuneKey &o) const
+    {
+        return std::tie(prec, N, lm, ld) < std::tie(o.prec, o.N, o.lm, o.ld);
+    }
+};
+static std::mutex g_tune_mu;
+static std::map<TuneKey, std::pair<int, double>> g_tune_cache;
+
+static int ilog2(int64_t x)
+{
+    int r = 0;
+    while (x > 1) { x >>= 1; ++r; }
+    return r;
+}
+
+static cudaError_t rebuild_schedules(Plan &p)
+{
+    for (auto &row : p.sched)
+        for (Schedule &s : row) free_schedule(s);
+    for (Schedule &s : p.sched_tc) free_schedule(s);
+    const int64_t before = p.max_partials;
+    cudaError_t e = build_schedules(p, hvp_on_tensor_cores(p.precision));
+    if (e != cudaSuccess) return e;
+    if (p.partials && p.max_partials > before) {
+        cudaFree(p.partials);
+        p.partials = nullptr;
+        e = dalloc(&p.partials, RED_SLOTS * p.max_partials);
+    }
+    return e;
+}
+
+static cudaError_t time_hvp(Plan &p, double *ms)
+{
+    cudaError_t e = launch_fill(p, p.p, 1.0 / double(p.N), p.M * p.N);
+    if (e != cudaSuccess) return e;
+    cudaEvent_t a, b;
+    if ((e = cudaEventCreate(&a)) != cudaSuccess) return e;
+    if ((e = cudaEventCreate(&b)) != cudaSuccess) { cudaEventDestroy(a); return e; }
+    double best = 1e30;
+    for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+        e = cudaEventRecord(a, p.stream);
+        if (e == cudaSuccess) {
+            if (hvp_on_tensor_cores(p.precision)) {
+                e = launch_hvp_tc(p, p.p, p.q, false, false);
+            } else {
+                e = launch_forward(p, prec_products(p.precision), FWD_STORE, p.p, p.O, nullptr, false);
+                if (e == cudaSuccess)
+                    e = launch_adjoint(p, prec_products(p.precision), ADJ_HESS, p.O, p.q, p.p, false);
+            }
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(b, p.stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(b);
+        float t = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, a, b);
+        if (rep > 0 && t < best) best = t;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    *ms = best;
+    return e;
+}
+
+static cudaError_t autotune(Plan &p)
+{
+    const bool tc = hvp_on_tensor_cores(p.precision);
+    const int64_t ncol = (p.N + band_bn(p.N) - 1) / band_bn(p.N);
+    const int full = int(std::max<int64_t>(1, p.num_sms / ncol));
+    std::vector<int> cand = tc ? std::vector<int>{full, std::max(1, 3 * full / 4), std::max(1, full / 2)}
+                               : std::vector<int>{1, 2, 4, 8};
+    const TuneKey key{p.precision, p.N, ilog2(p.M), ilog2(p.D)};
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            (tc ? p.tc_ctas : p.ups_simt) = it->second.first;
+            p.tuned = 1;
+            p.tuned_cached = 1;
+            p.tuned_ms = it->second.second;
+            return rebuild_schedules(p);
+        }
+    }
+    int best = cand[0];
+    double best_ms = 1e30;
+    for (int c : cand) {
+        (tc ? p.tc_ctas : p.ups_simt) = c;
+        cudaError_t e = rebuild_schedules(p);
+        double ms = 0.0;
+        if (e == cudaSuccess) e = time_hvp(p, &ms);
+        if (e != cudaSuccess) return e;
+        if (ms < best_ms) { best_ms = ms; best = c; }
+    }
+    (tc ? p.tc_ctas : p.ups_simt) = best;
+    p.tuned = 1;
+    p.tuned_ms = best_ms;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune_cache[key] = {best, best_ms};
+    }
+    return rebuild_schedules(p);
 }
 
 // R = F Theta - P in double, f = ||R||^2 + g(Theta) (Eq. min + Eq. regul).
@@ -397,7 +523,7 @@ tomo_status tomo_plan(tomo_plan_t *out, const tomo_desc *d)
     if (d->precision != TOMO_PREC_FP64 && d->precision != TOMO_PREC_FP32 &&
         d->precision != TOMO_PREC_MIXED && d->precision != TOMO_PREC_TC)
         return fail(TOMO_EINVAL, "unknown precision %d", d->precision);
-    if (d->flags != 0) return fail(TOMO_EINVAL, "flags must be 0");
+    if (d->flags & ~uint32_t(TOMO_PLAN_AUTOTUNE)) return fail(TOMO_EINVAL, "unknown flag bits");
     for (int64_t k = 0; k < d->D; ++k) {
         const double l = d->lambda[k];
         if (!std::isfinite(l) || l < 0.0) return fail(TOMO_EINVAL, "lambda[%lld] is not finite and >= 0", (long long)k);
@@ -473,6 +599,10 @@ tomo_status tomo_plan(tomo_plan_t *out, const tomo_desc *d)
     PLAN_TRY(cudaStreamSynchronize(p->stream));
     PLAN_TRY(build_schedules(*p, hvp_on_tensor_cores(p->precision)));
     PLAN_TRY(dalloc(&p->partials, RED_SLOTS * p->max_partials));
+    if (d->flags & TOMO_PLAN_AUTOTUNE) {
+        PLAN_TRY(autotune(*p));
+        PLAN_TRY(cudaStreamSynchronize(p->stream));
+    }
 #undef PLAN_TRY
     *out = reinterpret_cast<tomo_plan_t>(p);
     return TOMO_OK;
@@ -873,6 +1003,24 @@ tomo_status tomo_hvp(tomo_plan_t plan, const double *V, double *HV)
         CUDA_TRY(launch_adjoint(*p, prec_products(p->precision), ADJ_GRAD, p->O, HV, V, false));
     }
     CUDA_TRY(cudaStreamSynchronize(p->stream));
+    return TOMO_OK;
+}
+
+tomo_status tomo_plan_info(tomo_plan_t plan, tomo_plan_info_t *info)
+{
+    Plan *p = reinterpret_cast<Plan *>(plan);
+    if (!p || !info) return fail(TOMO_EINVAL, "NULL argument");
+    const bool tc = hvp_on_tensor_cores(p->precision);
+    info->autotuned = p->tuned;
+    info->from_cache = p->tuned_cached;
+    info->density = tc ? (p->tc_ctas > 0 ? p->tc_ctas : p->num_sms) : (p->ups_simt > 0 ? p->ups_simt : 4);
+    info->tensor_cores = tc ? 1 : 0;
+    info->hvp_ms = p->tuned_ms;
+    const int dbl = prec_products(p->precision) == TOMO_PREC_FP64 ? 1 : 0;
+    info->units_fwd = tc ? p->sched_tc[0].n_units : p->sched[0][dbl].n_units;
+    info->units_adj = tc ? p->sched_tc[1].n_units : p->sched[1][dbl].n_units;
+    info->ctas_fwd = tc ? p->sched_tc[0].n_ctas : p->sched[0][dbl].n_units;
+    info->ctas_adj = tc ? p->sched_tc[1].n_ctas : p->sched[1][dbl].n_units;
     return TOMO_OK;
 }
 

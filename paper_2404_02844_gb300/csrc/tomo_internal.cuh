@@ -74,6 +74,14 @@ struct Plan {
     bool own_stream;
     int device;
     int num_sms;
+    // schedule density of the band contractions: SIMT units per SM and
+    // column block, tensor-core persistent CTAs per column block (0: one per
+    // SM); chosen by the plan-time autotuner when asked
+    int ups_simt;
+    int tc_ctas;
+    int tuned;            // 1: the autotuner chose the density (timed or cached)
+    int tuned_cached;     // 1: taken from the per-process cache
+    double tuned_ms;      // Hessian-product time of the chosen density
 
     // problem tables (device)
     double *lam;       // D

@@ -72,7 +72,7 @@ def _desc(M=10, N=3, lam=None, gamma=0.0, prec=0, band_k=10.0, flags=0):
 
 
 @pytest.mark.parametrize("kw", [dict(M=0), dict(N=1), dict(N=2000), dict(gamma=-1.0),
-                                dict(gamma=float("nan")), dict(prec=7), dict(flags=1),
+                                dict(gamma=float("nan")), dict(prec=7), dict(flags=2),
                                 dict(lam=[0.0, 2.0, 1.0]), dict(lam=[0.0, float("inf")]),
                                 dict(lam=[-1.0, 2.0]), dict(band_k=float("nan"))])
 def test_invalid_descriptors_are_rejected_before_cuda(L, kw):

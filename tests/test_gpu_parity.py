@@ -399,3 +399,28 @@ def test_error_paths(tomo):
     with pytest.raises(tomo.TomoError) as e:
         tomo.Plan(10, 3, np.array([3.0, 1.0]), 10.0, 0.0)
     assert e.value.status == 1
+
+
+@pytest.mark.parametrize("prec", ["fp32", "tc"])
+def test_autotuned_plan_keeps_the_solution_and_caches_its_choice(tomo, prec):
+    w = workloads.small_case(M=300, bins=15, D=400, X=250.0, gamma=1e-2, seed=77)
+    P = dev(w.P)
+    with tomo.Plan.from_workload(w, precision=prec) as plain:
+        Th0, r0 = plain.fit(P, eps_kkt=1e-10, max_newton=600)
+        f0 = plain.objective(P, Th0)
+        info0 = plain.info()
+    with tomo.Plan.from_workload(w, precision=prec, autotune=True) as tuned:
+        info = tuned.info()
+        Th1, r1 = tuned.fit(P, eps_kkt=1e-10, max_newton=600)
+        f1 = tuned.objective(P, Th1)
+    assert info0["autotuned"] == 0 and info["autotuned"] == 1
+    assert info["hvp_ms"] > 0.0
+    if prec == "tc":
+        assert info["tensor_cores"] == 1 and 1 <= info["density"] <= info0["density"]
+    else:
+        assert info["density"] in (1, 2, 4, 8)
+    assert abs(f1 - f0) <= 1e-8 * f0, (f0, f1)
+    # a second plan of the same class takes the cached choice
+    with tomo.Plan.from_workload(w, precision=prec, autotune=True) as again:
+        info2 = again.info()
+    assert info2["from_cache"] == 1 and info2["density"] == info["density"]
