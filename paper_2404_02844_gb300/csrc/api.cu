@@ -401,6 +401,15 @@ static cudaError_t rebuild_schedules(Plan &p)
 static cudaError_t time_hvp(Plan &p, double *ms)
 {
     cudaError_t e = launch_fill(p, p.p, 1.0 / double(p.N), p.M * p.N);
+    // float input of the tensor-core form: 1/N in every float, written as
+    // doubles whose two halves are that float
+    const float f = 1.0f / float(p.N);
+    uint32_t fb;
+    std::memcpy(&fb, &f, sizeof(fb));
+    const uint64_t pair = (uint64_t(fb) << 32) | uint64_t(fb);
+    double dpair;
+    std::memcpy(&dpair, &pair, sizeof(dpair));
+    if (e == cudaSuccess) e = launch_fill(p, p.u, dpair, (p.M * p.N + 1) / 2);
     if (e != cudaSuccess) return e;
     cudaEvent_t a, b;
     if ((e = cudaEventCreate(&a)) != cudaSuccess) return e;
@@ -410,7 +419,8 @@ static cudaError_t time_hvp(Plan &p, double *ms)
         e = cudaEventRecord(a, p.stream);
         if (e == cudaSuccess) {
             if (hvp_on_tensor_cores(p.precision)) {
-                e = launch_hvp_tc(p, p.p, p.q, false, false);
+                // the CG's float vectors (the first half of the double buffers)
+                e = launch_hvp_tc(p, p.u, p.q, true, false);
             } else {
                 e = launch_forward(p, prec_products(p.precision), FWD_STORE, p.p, p.O, nullptr, false);
                 if (e == cudaSuccess)

@@ -461,26 +461,42 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(TcArgs a)
             __threadfence();
             // each thread sums P4 float4 columns of the tile over the splits,
             // split by split (P4 independent loads in flight per thread)
+            // the splits' loads are software-pipelined (the next split's loads
+            // are in flight while the current one is added), in halves of at
+            // most 8 float4 per thread to bound the registers
             constexpr int P4 = TE / 4 / TC_THREADS;
-            static_assert(TE % (4 * TC_THREADS) == 0, "tile divides into float4 per thread");
-            float4 acc4[P4];
+            constexpr int PH = P4 < 8 ? P4 : 8;
+            static_assert(TE % (4 * TC_THREADS) == 0 && P4 % PH == 0, "tile divides into float4 per thread");
+#pragma unroll 1
+            for (int h0 = 0; h0 < P4; h0 += PH) {
+                float4 acc4[PH], cur[PH];
 #pragma unroll
-            for (int j = 0; j < P4; ++j) acc4[j] = make_float4(0.f, 0.f, 0.f, 0.f);
-            for (int sidx = 0; sidx < nsplit; ++sidx) {
-                const float4 *src = reinterpret_cast<const float4 *>(base + sidx * split_stride);
-                float4 t[P4];
-#pragma unroll
-                for (int j = 0; j < P4; ++j) t[j] = __ldcg(src + tid + j * TC_THREADS);
-#pragma unroll
-                for (int j = 0; j < P4; ++j) {
-                    acc4[j].x += t[j].x; acc4[j].y += t[j].y; acc4[j].z += t[j].z; acc4[j].w += t[j].w;
+                for (int j = 0; j < PH; ++j) {
+                    acc4[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    cur[j] = __ldcg(reinterpret_cast<const float4 *>(base) + tid + (h0 + j) * TC_THREADS);
                 }
-            }
+                for (int sidx = 0; sidx < nsplit; ++sidx) {
+                    float4 nxt[PH];
+                    if (sidx + 1 < nsplit) {
+                        const float4 *src = reinterpret_cast<const float4 *>(base + (sidx + 1) * split_stride);
 #pragma unroll
-            for (int j = 0; j < P4; ++j) {
-                const int e = (tid + j * TC_THREADS) * 4, rr = e / BN, cc = e % BN;
-                float *d = &tile_s[rr * LD + cc];
-                d[0] = acc4[j].x; d[1] = acc4[j].y; d[2] = acc4[j].z; d[3] = acc4[j].w;
+                        for (int j = 0; j < PH; ++j) nxt[j] = __ldcg(src + tid + (h0 + j) * TC_THREADS);
+                    }
+#pragma unroll
+                    for (int j = 0; j < PH; ++j) {
+                        acc4[j].x += cur[j].x; acc4[j].y += cur[j].y; acc4[j].z += cur[j].z; acc4[j].w += cur[j].w;
+                    }
+                    if (sidx + 1 < nsplit) {
+#pragma unroll
+                        for (int j = 0; j < PH; ++j) cur[j] = nxt[j];
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < PH; ++j) {
+                    const int e = (tid + (h0 + j) * TC_THREADS) * 4, rr = e / BN, cc = e % BN;
+                    float *d = &tile_s[rr * LD + cc];
+                    d[0] = acc4[j].x; d[1] = acc4[j].y; d[2] = acc4[j].z; d[3] = acc4[j].w;
+                }
             }
             __syncthreads();
         }
@@ -498,8 +514,111 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(TcArgs a)
             a.o_lo[n * a.opitch + grow] = __float2bfloat16_rn(v - __bfloat162float(h));
         }
     }
-    if (!FWD && owner) {
-        // q = 2 Z + 2 gamma L u along rows
+    if (!FWD && owner && a.vec_f32 && (a.N % 4) == 0) {
+        // q = 2 Z + 2 gamma L u, float vectors: a thread takes 4 consecutive
+        // columns (float4) of TILE_R / RPI rows, and the loads of UNR rows
+        // are all issued before any of them is used (memory-level
+        // parallelism: this epilogue runs once per tile, on the critical path)
+        constexpr int CG = BN / 4;                 // float4 column groups per row
+        constexpr int RPI = TC_THREADS / CG;       // rows per pass
+        constexpr int PASSES = TILE_R / RPI;
+        constexpr int UNR = 4;
+        static_assert(PASSES % UNR == 0, "passes divide by the unroll");
+        const float g2f = float(2.0 * a.gamma);
+        const float *u = static_cast<const float *>(a.u);
+        float *q = static_cast<float *>(a.q);
+        const int cc = (tid % CG) * 4;
+        const int64_t n = n0 + cc;
+        for (int p0 = 0; p0 < PASSES; p0 += UNR) {
+            float4 uc[UNR], ud[UNR], uu[UNR];
+#pragma unroll
+            for (int j = 0; j < UNR; ++j) {
+                const int rr = (p0 + j) * RPI + tid / CG;
+                const int64_t grow = r0 + rr;
+                const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                uc[j] = ud[j] = uu[j] = z4;
+                if (grow < a.M && n < a.N && g2f != 0.f) {
+                    const float4 *row = reinterpret_cast<const float4 *>(u + grow * a.N + n);
+                    uc[j] = *row;
+                    if (grow < a.M - 1) ud[j] = *reinterpret_cast<const float4 *>(u + (grow + 1) * a.N + n);
+                    if (grow > 0) uu[j] = *reinterpret_cast<const float4 *>(u + (grow - 1) * a.N + n);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < UNR; ++j) {
+                const int rr = (p0 + j) * RPI + tid / CG;
+                const int64_t grow = r0 + rr;
+                if (grow >= a.M || n >= a.N) continue;
+                const bool has_d = grow < a.M - 1, has_u = grow > 0;
+                const float *zr = &tile_s[rr * LD + cc];
+                float4 o;
+                o.x = fmaf(g2f, (has_d ? uc[j].x - ud[j].x : 0.f) + (has_u ? uc[j].x - uu[j].x : 0.f), 2.f * zr[0]);
+                o.y = fmaf(g2f, (has_d ? uc[j].y - ud[j].y : 0.f) + (has_u ? uc[j].y - uu[j].y : 0.f), 2.f * zr[1]);
+                o.z = fmaf(g2f, (has_d ? uc[j].z - ud[j].z : 0.f) + (has_u ? uc[j].z - uu[j].z : 0.f), 2.f * zr[2]);
+                o.w = fmaf(g2f, (has_d ? uc[j].w - ud[j].w : 0.f) + (has_u ? uc[j].w - uu[j].w : 0.f), 2.f * zr[3]);
+                *reinterpret_cast<float4 *>(q + grow * a.N + n) = o;
+            }
+        }
+    } else if (!FWD && owner && !a.vec_f32 && (a.N % 4) == 0) {
+        // the same for double vectors (two double2 per 4 columns)
+        constexpr int CG = BN / 4;
+        constexpr int RPI = TC_THREADS / CG;
+        constexpr int PASSES = TILE_R / RPI;
+        constexpr int UNR = 4;
+        const double g2 = 2.0 * a.gamma;
+        const double *u = static_cast<const double *>(a.u);
+        double *q = static_cast<double *>(a.q);
+        const int cc = (tid % CG) * 4;
+        const int64_t n = n0 + cc;
+        for (int p0 = 0; p0 < PASSES; p0 += UNR) {
+            double2 uc[UNR][2], ud[UNR][2], uu[UNR][2];
+#pragma unroll
+            for (int j = 0; j < UNR; ++j) {
+                const int rr = (p0 + j) * RPI + tid / CG;
+                const int64_t grow = r0 + rr;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) uc[j][h] = ud[j][h] = uu[j][h] = make_double2(0.0, 0.0);
+                if (grow < a.M && n < a.N && g2 != 0.0) {
+                    const double2 *c0 = reinterpret_cast<const double2 *>(u + grow * a.N + n);
+                    uc[j][0] = c0[0];
+                    uc[j][1] = c0[1];
+                    if (grow < a.M - 1) {
+                        const double2 *d0 = reinterpret_cast<const double2 *>(u + (grow + 1) * a.N + n);
+                        ud[j][0] = d0[0];
+                        ud[j][1] = d0[1];
+                    }
+                    if (grow > 0) {
+                        const double2 *u0 = reinterpret_cast<const double2 *>(u + (grow - 1) * a.N + n);
+                        uu[j][0] = u0[0];
+                        uu[j][1] = u0[1];
+                    }
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < UNR; ++j) {
+                const int rr = (p0 + j) * RPI + tid / CG;
+                const int64_t grow = r0 + rr;
+                if (grow >= a.M || n >= a.N) continue;
+                const bool has_d = grow < a.M - 1, has_u = grow > 0;
+                const float *zr = &tile_s[rr * LD + cc];
+                double out[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const double xc = c & 1 ? uc[j][c >> 1].y : uc[j][c >> 1].x;
+                    const double xd = c & 1 ? ud[j][c >> 1].y : ud[j][c >> 1].x;
+                    const double xu = c & 1 ? uu[j][c >> 1].y : uu[j][c >> 1].x;
+                    double lx = 0.0;
+                    if (has_d) lx += xc - xd;
+                    if (has_u) lx += xc - xu;
+                    out[c] = 2.0 * double(zr[c]) + g2 * lx;
+                }
+                double2 *qo = reinterpret_cast<double2 *>(q + grow * a.N + n);
+                qo[0] = make_double2(out[0], out[1]);
+                qo[1] = make_double2(out[2], out[3]);
+            }
+        }
+    } else if (!FWD && owner) {
+        // q = 2 Z + 2 gamma L u along rows (N not a multiple of 4)
         const double g2 = 2.0 * a.gamma;
         const float g2f = float(g2);
         for (int e = tid; e < TE; e += TC_THREADS) {
