@@ -574,7 +574,9 @@ tomo_status tomo_plan(tomo_plan_t *out, const tomo_desc *d)
     const int64_t M = p->M, N = p->N, D = p->D, MN = M * N, DN = D * N;
     p->fwd_tiles = int((D + TILE_R - 1) / TILE_R);
     p->adj_tiles = int((M + TILE_R - 1) / TILE_R);
-    p->max_partials = int64_t(p->num_sms) * 8;  // row kernels; raised by the schedules
+    // row kernels and the per-tile partials of the fused CG restriction;
+    // raised by the schedules
+    p->max_partials = std::max<int64_t>(int64_t(p->num_sms) * 8, p->adj_tiles);
 
     PLAN_TRY(dalloc(&p->lam, D));
     PLAN_TRY(dalloc(&p->lo, D));
@@ -693,7 +695,7 @@ static tomo_status cg_chunk(Plan &p, int stage, int count, const ChunkEvents *ev
         if (tc) {
             // tensor cores: the whole Hessian product (forward + adjoint) is
             // timed as the "forward" interval, the adjoint interval is empty
-            CUDA_TRY(launch_hvp_tc(p, in, p.q, p.cg_f32, true));
+            CUDA_TRY(launch_hvp_tc(p, in, p.q, p.cg_f32, true, stage));
             if (evs) CUDA_TRY(cudaEventRecordWithFlags(evs->ev[c][1], p.stream, evflag));
         } else {
             CUDA_TRY(launch_forward(p, prec_products(p.precision), FWD_STORE, in, p.O, nullptr, true));
@@ -701,7 +703,8 @@ static tomo_status cg_chunk(Plan &p, int stage, int count, const ChunkEvents *ev
             CUDA_TRY(launch_adjoint(p, prec_products(p.precision), ADJ_HESS, p.O, p.q, in, true));
         }
         if (evs) CUDA_TRY(cudaEventRecordWithFlags(evs->ev[c][2], p.stream, evflag));
-        CUDA_TRY(launch_cg_restrict(p, stage));
+        // the tensor-core adjoint applies the restriction itself when it can
+        if (!(tc && tc_restrict_fusable(p))) CUDA_TRY(launch_cg_restrict(p, stage));
         CUDA_TRY(launch_cg_update_xr(p, stage));
         CUDA_TRY(launch_cg_update_p(p, stage));
     }

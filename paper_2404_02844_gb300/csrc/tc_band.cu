@@ -54,7 +54,7 @@ struct TcLayout {
                                  META_BYTES + RINV_BYTES;
     static constexpr int TMEM_COLS = BN < 32 ? 32 : BN;
     static_assert(TOTAL <= 227 * 1024, "shared memory per CTA");
-    static_assert(TILE_R * (BN + 1) * 4 <= STAGE_BYTES, "epilogue tile fits the stage buffers");
+    static_assert(TILE_R * (BN + 1) * 4 + TILE_R * 4 <= STAGE_BYTES, "epilogue tile and row values fit the stage buffers");
 };
 
 struct TcArgs {
@@ -84,6 +84,19 @@ struct TcArgs {
     const void *u;
     int vec_f32;
     double gamma;
+    // CG restriction fused into the adjoint epilogue (float vectors, one
+    // column block, N % 4 == 0): q <- q - q_{i,m(i)} (stage 2) on the free
+    // variables, 0 elsewhere, and p^T q; each tile's owner writes its partial
+    // dot and the last tile sums them in tile order and sets alpha = rz / pq
+    // (or stops the CG on non-positive curvature)
+    int restrict_stage;           // 0: off, 1 or 2: the CG stage
+    const uint8_t *freem;
+    const int32_t *mrow;
+    const float *pvec;
+    double *pq_part;              // one per adjoint tile
+    unsigned int *pq_ticket;
+    DevScalars *sc;
+    int n_tiles;
 };
 
 // Float weights of the run of 8 photon numbers i_r.. of probe d (zero outside
@@ -503,15 +516,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(TcArgs a)
     }
     if (FWD && owner) {
         // O^T hi/lo copies for the adjoint's operand B: consecutive threads
-        // take consecutive probes of one outcome column
-        for (int e = tid; e < TE; e += TC_THREADS) {
-            const int nl = e / TILE_R, rr = e % TILE_R;
+        // take consecutive pairs of probes of one outcome column (one 4-byte
+        // store per part; the row offset r0 and the pitch are even)
+        for (int e = tid; e < TE / 2; e += TC_THREADS) {
+            const int nl = e / (TILE_R / 2), rr = (e % (TILE_R / 2)) * 2;
             const int64_t grow = r0 + rr, n = n0 + nl;
             if (grow >= a.D || n >= a.N) continue;
-            const float v = tile_s[rr * LD + nl];
-            const __nv_bfloat16 h = __float2bfloat16_rn(v);
-            a.o_hi[n * a.opitch + grow] = h;
-            a.o_lo[n * a.opitch + grow] = __float2bfloat16_rn(v - __bfloat162float(h));
+            const float v0 = tile_s[rr * LD + nl];
+            const float v1 = grow + 1 < a.D ? tile_s[(rr + 1) * LD + nl] : 0.f;
+            const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+            const float2 hf = __bfloat1622float2(h);
+            const __nv_bfloat162 l = __floats2bfloat162_rn(v0 - hf.x, v1 - hf.y);
+            if (grow + 1 < a.D) {
+                *reinterpret_cast<__nv_bfloat162 *>(a.o_hi + n * a.opitch + grow) = h;
+                *reinterpret_cast<__nv_bfloat162 *>(a.o_lo + n * a.opitch + grow) = l;
+            } else {
+                a.o_hi[n * a.opitch + grow] = h.x;
+                a.o_lo[n * a.opitch + grow] = l.x;
+            }
         }
     }
     if (!FWD && owner && a.vec_f32 && (a.N % 4) == 0) {
@@ -529,14 +551,41 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(TcArgs a)
         float *q = static_cast<float *>(a.q);
         const int cc = (tid % CG) * 4;
         const int64_t n = n0 + cc;
+        const int rstage = a.restrict_stage;
+        float *qm_s = tile_s + TILE_R * LD;        // per-row q_{i,m(i)} (stage 2)
+        if (rstage != 0) {
+            if (tid < TILE_R) {
+                const int64_t grow = r0 + tid;
+                float qm = 0.f;
+                if (rstage == 2 && grow < a.M) {
+                    const int m = a.mrow[grow];
+                    float lx = 0.f;
+                    if (g2f != 0.f) {
+                        const float xc = u[grow * a.N + m];
+                        if (grow < a.M - 1) lx += xc - u[(grow + 1) * a.N + m];
+                        if (grow > 0) lx += xc - u[(grow - 1) * a.N + m];
+                    }
+                    qm = fmaf(g2f, lx, 2.f * tile_s[tid * LD + (m - int(n0))]);
+                }
+                qm_s[tid] = qm;
+            }
+            __syncthreads();
+        }
+        float pq_acc = 0.f;
         for (int p0 = 0; p0 < PASSES; p0 += UNR) {
-            float4 uc[UNR], ud[UNR], uu[UNR];
+            float4 uc[UNR], ud[UNR], uu[UNR], pv[UNR];
+            uchar4 fm[UNR];
 #pragma unroll
             for (int j = 0; j < UNR; ++j) {
                 const int rr = (p0 + j) * RPI + tid / CG;
                 const int64_t grow = r0 + rr;
                 const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-                uc[j] = ud[j] = uu[j] = z4;
+                uc[j] = ud[j] = uu[j] = pv[j] = z4;
+                fm[j] = make_uchar4(0, 0, 0, 0);
+                if (rstage != 0 && grow < a.M && n < a.N) {
+                    fm[j] = *reinterpret_cast<const uchar4 *>(a.freem + grow * a.N + n);
+                    pv[j] = *reinterpret_cast<const float4 *>(a.pvec + grow * a.N + n);
+                }
                 if (grow < a.M && n < a.N && g2f != 0.f) {
                     const float4 *row = reinterpret_cast<const float4 *>(u + grow * a.N + n);
                     uc[j] = *row;
@@ -556,7 +605,57 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(TcArgs a)
                 o.y = fmaf(g2f, (has_d ? uc[j].y - ud[j].y : 0.f) + (has_u ? uc[j].y - uu[j].y : 0.f), 2.f * zr[1]);
                 o.z = fmaf(g2f, (has_d ? uc[j].z - ud[j].z : 0.f) + (has_u ? uc[j].z - uu[j].z : 0.f), 2.f * zr[2]);
                 o.w = fmaf(g2f, (has_d ? uc[j].w - ud[j].w : 0.f) + (has_u ? uc[j].w - uu[j].w : 0.f), 2.f * zr[3]);
+                if (rstage != 0) {
+                    const float qm = qm_s[rr];
+                    o.x = fm[j].x ? o.x - qm : 0.f;
+                    o.y = fm[j].y ? o.y - qm : 0.f;
+                    o.z = fm[j].z ? o.z - qm : 0.f;
+                    o.w = fm[j].w ? o.w - qm : 0.f;
+                    pq_acc = fmaf(pv[j].x, o.x, pq_acc);
+                    pq_acc = fmaf(pv[j].y, o.y, pq_acc);
+                    pq_acc = fmaf(pv[j].z, o.z, pq_acc);
+                    pq_acc = fmaf(pv[j].w, o.w, pq_acc);
+                }
                 *reinterpret_cast<float4 *>(q + grow * a.N + n) = o;
+            }
+        }
+        if (rstage != 0) {
+            // the tile's partial p^T q (double across threads, fixed tree),
+            // then the last tile's owner finishes the dot in tile order
+            __shared__ double red_s[TC_THREADS / 32];
+            __shared__ int last_tile;
+            double v = double(pq_acc);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) red_s[warp] = v;
+            __syncthreads();
+            if (tid == 0) {
+                double t = 0.0;
+                for (int w = 0; w < TC_THREADS / 32; ++w) t += red_s[w];
+                a.pq_part[tile] = t;
+                __threadfence();
+                last_tile = atomicAdd(a.pq_ticket, 1u) == unsigned(a.n_tiles - 1);
+            }
+            __syncthreads();
+            if (last_tile) {
+                __threadfence();
+                double t = 0.0;
+                for (int k = tid; k < a.n_tiles; k += TC_THREADS) t += __ldcg(&a.pq_part[k]);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+                __syncthreads();
+                if (lane == 0) red_s[warp] = t;
+                __syncthreads();
+                if (tid == 0) {
+                    double pq = 0.0;
+                    for (int w = 0; w < TC_THREADS / 32; ++w) pq += red_s[w];
+                    DevScalars *sc = a.sc;
+                    sc->pq = pq;
+                    if (!(pq > 0.0)) sc->cg_active = 0;
+                    else sc->alpha = sc->rz / pq;
+                    *a.pq_ticket = 0u;
+                    __threadfence();
+                }
             }
         }
     } else if (!FWD && owner && !a.vec_f32 && (a.N % 4) == 0) {
@@ -736,13 +835,24 @@ static TcArgs tc_args(Plan &p, bool fwd, const int32_t *gate)
     a.o_hi = p.ot_hi; a.o_lo = p.ot_lo; a.opitch = p.ot_pitch;
     a.q = nullptr; a.u = nullptr; a.vec_f32 = 0;
     a.gamma = p.gamma;
+    a.restrict_stage = 0;
+    a.freem = p.freem; a.mrow = p.mrow; a.pvec = reinterpret_cast<const float *>(p.p);
+    a.pq_part = p.partials + 3 * p.max_partials;
+    a.pq_ticket = &p.sc->ticket[1];
+    a.sc = p.sc;
+    a.n_tiles = p.adj_tiles;
     return a;
 }
 
 // HV = 2 F^T (F V) + 2 gamma L V on the tensor cores (three launches: the
 // transposed split copy of V, the forward tile product, the adjoint tile
 // product with the smoothness term).
-cudaError_t launch_hvp_tc(Plan &p, const void *V, void *HV, bool vec_f32, bool gated)
+bool tc_restrict_fusable(const Plan &p)
+{
+    return p.cg_f32 && band_bn(p.N) >= p.N && (p.N % 4) == 0;
+}
+
+cudaError_t launch_hvp_tc(Plan &p, const void *V, void *HV, bool vec_f32, bool gated, int restrict_stage)
 {
     const int32_t *gate = gated ? &p.sc->cg_active : nullptr;
     dim3 tb(32, 8), tg(unsigned((p.M + 31) / 32), unsigned((p.N + 31) / 32));
@@ -761,6 +871,7 @@ cudaError_t launch_hvp_tc(Plan &p, const void *V, void *HV, bool vec_f32, bool g
     b.q = HV;
     b.u = V;
     b.vec_f32 = vec_f32 ? 1 : 0;
+    b.restrict_stage = (vec_f32 && tc_restrict_fusable(p)) ? restrict_stage : 0;
     return launch_tc<false>(p, b);
 }
 

@@ -183,7 +183,10 @@ inline bool hvp_on_tensor_cores(int precision) { return precision == TOMO_PREC_T
 
 // tc_band.cu
 // V, HV: float when vec_f32 (the CG vectors of the tensor-core form), else double
-cudaError_t launch_hvp_tc(Plan &p, const void *V, void *HV, bool vec_f32, bool gated);
+// restrict_stage 1 or 2 also applies the CG restriction of that stage to HV
+// and finishes p^T q and alpha (float vectors, when tc_restrict_fusable)
+cudaError_t launch_hvp_tc(Plan &p, const void *V, void *HV, bool vec_f32, bool gated, int restrict_stage = 0);
+bool tc_restrict_fusable(const Plan &p);
 size_t tc_smem_bytes(int bn);
 
 // records a failure message for tomo_last_error (api.cu)
