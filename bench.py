@@ -38,6 +38,11 @@ UNIT = "POVM-elem*iters/s"
 GAP = 1e-8
 CHOSEN = "tc"
 REF_ITERS = 4
+# DRAM bytes (read + write) of one tensor-core Hessian product, forward +
+# adjoint band contraction, from `ncu --set full` on the late-phase CG of the
+# c2 workload (profiles/k_band_tc_c2_hvp.md); the transpose kernel is not
+# included.  Must be reset to None whenever k_band_tc changes.
+TC_HVP_DRAM_BYTES = 5.136896e6 + 12.264704e6
 WORKLOAD = "c2: M=4096 N=128 D=8192, 127-bin eta=0.8 dark=1e-4, lambda lin [0,3000], 1e7 shots, gamma=1e-2, band +-10sqrt(lambda)"
 
 
@@ -268,7 +273,8 @@ def main():
         bound, peak_src = "alu", f"{sms} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz"
     achieved = flops / (hvp_ms * 1e-3) / 1e12
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": TC_HVP_DRAM_BYTES if CHOSEN == "tc" else None,
+                "traffic_unit": "bytes per Hessian product (ncu dram read+write, forward+adjoint)",
                 "kernel": "CG Hessian product: k_transpose_split + k_band_tc<fwd> + k_band_tc<adj>",
                 "avg_launch_ms": hvp_ms, "algorithmic_flops_per_launch": flops,
                 "peak_source": peak_src,
