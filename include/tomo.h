@@ -245,6 +245,14 @@ tomo_status tomo_project_simplex(tomo_plan_t plan, const double *X, double *Y);
  * Uses plan workspaces: not concurrent with another call on the same plan. */
 tomo_status tomo_smooth(tomo_plan_t plan, const double *X, double *Y, int64_t exclude, double div);
 
+/* Infidelity 1 - F_n of Eq. fidelities between two POVMs (M x N doubles,
+ * device, row-major; each column an operator diagonal in the photon-number
+ * basis): F_n = (sum_i sqrt(Theta_in Ref_in))^2 / (sum_i Theta_in sum_i Ref_in),
+ * the matrix-square-root definition for commuting operators.  infid_host
+ * receives N doubles (nan for an all-zero column).  Uses plan workspaces. */
+tomo_status tomo_infidelity(tomo_plan_t plan, const double *Theta, const double *Theta_ref,
+                            double *infid_host);
+
 /* KKT residual of App. B for (Theta, G), both M x N device; double. */
 tomo_status tomo_kkt(tomo_plan_t plan, const double *Theta, const double *G,
                      double *kkt_host);

@@ -287,3 +287,17 @@ class Problem:
                            ctypes.byref(rep), _p(hist))
         r = {k: getattr(rep, k) for k, _ in _Report._fields_}
         return Th, r, hist[:nh].copy()
+
+
+def infidelity(Theta, Theta_ref):
+    """Per-outcome infidelity 1 - F_n of Eq. fidelities for phase-insensitive
+    (diagonal) POVMs: the operators commute, so
+    Tr((sqrt(pi) pi_ref sqrt(pi))^(1/2)) = sum_i sqrt(Theta_in Theta_ref_in) and
+    F_n = (sum_i sqrt(Theta_in Theta_ref_in))^2 / (sum_i Theta_in sum_i Theta_ref_in).
+    Outcomes with an all-zero column on either side give nan."""
+    A = np.asarray(Theta, dtype=np.float64)
+    B = np.asarray(Theta_ref, dtype=np.float64)
+    num = np.sum(np.sqrt(A * B), axis=0) ** 2
+    den = A.sum(axis=0) * B.sum(axis=0)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        return 1.0 - num / den

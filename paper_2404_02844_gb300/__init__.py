@@ -91,6 +91,7 @@ EXPORTS = [
     ("tomo_plan_info", c_i32, [c_ptr, ctypes.POINTER(tomo_plan_info_t)]),
     ("tomo_project_simplex", c_i32, [c_ptr, c_ptr, c_ptr]),
     ("tomo_smooth", c_i32, [c_ptr, c_ptr, c_ptr, c_i64, c_dbl]),
+    ("tomo_infidelity", c_i32, [c_ptr, c_ptr, c_ptr, c_ptr]),
     ("tomo_kkt", c_i32, [c_ptr, c_ptr, c_ptr, ctypes.POINTER(c_dbl)]),
     ("tomo_poisson_weights", c_i32, [c_ptr, c_ptr, c_ptr, c_i64, c_ptr]),
     ("tomo_bands", c_i32, [c_ptr, c_ptr, c_ptr]),
@@ -410,6 +411,13 @@ class Plan:
         o["start_stage"] = 2
         Th, rep2 = self.fit(P, Th, **o)
         return Th, rep1, rep2
+
+    def infidelity(self, Theta, Theta_ref) -> np.ndarray:
+        """Per-outcome infidelity 1 - F_n (Eq. fidelities) of two POVMs."""
+        out = np.empty(self.N)
+        _check(lib().tomo_infidelity(self._h, _ptr(Theta), _ptr(Theta_ref), out.ctypes.data),
+               "tomo_infidelity")
+        return out
 
     def kkt(self, Theta, G):
         return tomo_kkt(self._h, _ptr(Theta), _ptr(G))

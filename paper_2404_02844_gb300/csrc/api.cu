@@ -1065,6 +1065,16 @@ tomo_status tomo_smooth(tomo_plan_t plan, const double *X, double *Y, int64_t ex
     return TOMO_OK;
 }
 
+tomo_status tomo_infidelity(tomo_plan_t plan, const double *Theta, const double *Theta_ref, double *infid_host)
+{
+    Plan *p = reinterpret_cast<Plan *>(plan);
+    if (!p || !Theta || !Theta_ref || !infid_host) return fail(TOMO_EINVAL, "NULL argument");
+    CUDA_TRY(launch_infidelity(*p, Theta, Theta_ref, p->O));
+    CUDA_TRY(cudaMemcpyAsync(infid_host, p->O, sizeof(double) * size_t(p->N), cudaMemcpyDeviceToHost, p->stream));
+    CUDA_TRY(cudaStreamSynchronize(p->stream));
+    return TOMO_OK;
+}
+
 tomo_status tomo_kkt(tomo_plan_t plan, const double *Theta, const double *G, double *kkt_host)
 {
     Plan *p = reinterpret_cast<Plan *>(plan);

@@ -143,3 +143,64 @@ cudaError_t launch_smooth(Plan &p, const double *X, double *Y, int64_t exclude, 
 }
 
 }  // namespace tomo
+
+// ---------------------------------------------------------------------------
+// Infidelity of two phase-insensitive POVMs (Eq. fidelities), per outcome n:
+// the operators are diagonal in the photon-number basis, so
+//   F_n = (sum_i sqrt(A_in B_in))^2 / (sum_i A_in  sum_i B_in),
+// and the result is 1 - F_n.  Two launches: per-CTA column sums of
+// sqrt(A B), A and B over a block of rows (threads along the row, coalesced),
+// then one thread per outcome adds the CTAs' sums in CTA order.
+// ---------------------------------------------------------------------------
+namespace tomo {
+
+__global__ void __launch_bounds__(256)
+k_fid_partials(int64_t M, int64_t N, int64_t rows_per_cta, const double *A, const double *B, double *part)
+{
+    const int64_t i0 = int64_t(blockIdx.x) * rows_per_cta;
+    const int64_t i1 = i0 + rows_per_cta < M ? i0 + rows_per_cta : M;
+    for (int64_t n = threadIdx.x; n < N; n += blockDim.x) {
+        double sab = 0.0, sa = 0.0, sb = 0.0;
+        for (int64_t i = i0; i < i1; ++i) {
+            const double a = A[i * N + n], b = B[i * N + n];
+            sab += sqrt(a * b);
+            sa += a;
+            sb += b;
+        }
+        double *o = part + int64_t(blockIdx.x) * 3 * N;
+        o[n] = sab;
+        o[N + n] = sa;
+        o[2 * N + n] = sb;
+    }
+}
+
+__global__ void k_fid_final(int64_t N, int64_t ctas, const double *part, double *out)
+{
+    const int64_t n = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (n >= N) return;
+    double sab = 0.0, sa = 0.0, sb = 0.0;
+    for (int64_t c = 0; c < ctas; ++c) {
+        sab += part[c * 3 * N + n];
+        sa += part[c * 3 * N + N + n];
+        sb += part[c * 3 * N + 2 * N + n];
+    }
+    out[n] = 1.0 - (sab * sab) / (sa * sb);
+}
+
+cudaError_t launch_infidelity(Plan &p, const double *A, const double *B, double *out_dev)
+{
+    const int64_t M = p.M, N = p.N;
+    // 3 N partial sums per CTA: in the M x N workspace s when 3 ctas <= M,
+    // else (tiny M: one CTA) in the reduction partials (>= 4 x 1216 doubles)
+    int64_t ctas = int64_t(p.num_sms) * 4;
+    if (3 * ctas > M) ctas = M / 3 > 0 ? M / 3 : 1;
+    const int64_t rows = (M + ctas - 1) / ctas;
+    ctas = (M + rows - 1) / rows;
+    double *part = (3 * ctas <= M) ? p.s : p.partials;
+    k_fid_partials<<<unsigned(ctas), 256, 0, p.stream>>>(M, N, rows, A, B, part);
+    k_fid_final<<<unsigned((N + 127) / 128), 128, 0, p.stream>>>(N, ctas, part, out_dev);
+    count_launch(2);
+    return cudaGetLastError();
+}
+
+}  // namespace tomo

@@ -167,6 +167,7 @@ cudaError_t launch_trial(Plan &p, int stage, double alpha, bool delta_mode);
 cudaError_t launch_set_grad_dir(Plan &p);
 // smooth.cu
 cudaError_t launch_smooth(Plan &p, const double *X, double *Y, int64_t exclude, double div);
+cudaError_t launch_infidelity(Plan &p, const double *A, const double *B, double *out_dev);
 cudaError_t launch_nonfinite_check(Plan &p, const double *x, int64_t n, int slot);
 
 int band_bn(int64_t N);

@@ -297,3 +297,61 @@ def c5_batch(js, F=None, C0: int = C5_C0, **kw):
         T[b, :, :w.N] = w.theta_true
         nc[b] = w.N
     return P, T, nc, ws
+
+
+# ---- the paper's detector geometry (time-multiplexed loop detector) --------
+# Sec. Experiment: out-coupling R, loop efficiency eta_loop, detector
+# efficiency eta_det fitted by the paper; 150 time bins (N = 151 outcomes);
+# D = 1076 coherent probes with |alpha_d|^2 ~ d^2; Hilbert space M = 1210581;
+# 5e5 trials per probe.
+LOOP_R, LOOP_ETA_LOOP, LOOP_ETA_DET = 0.91644, 0.90524, 0.528
+F2_M, F2_D, F2_BINS, F2_SHOTS = 1210581, 1076, 150, 500_000
+
+
+def loop_bin_click(bins: int = F2_BINS, R: float = LOOP_R, eta_loop: float = LOOP_ETA_LOOP,
+                   eta_det: float = LOOP_ETA_DET) -> np.ndarray:
+    """Per-photon click probability of time bin j = 1..bins (Eq. pj_fock at
+    i = 1): q_1 = R eta_det, q_j = (1 - R)^2 R^-1 (R eta_loop)^(j-1) eta_det."""
+    j = np.arange(1, bins + 1, dtype=np.float64)
+    q = (1.0 - R) ** 2 / R * (R * eta_loop) ** (j - 1) * eta_det
+    q[0] = R * eta_det
+    return q
+
+
+def loop_detector_povm(M: int, bins: int = F2_BINS, R: float = LOOP_R, eta_loop: float = LOOP_ETA_LOOP,
+                       eta_det: float = LOOP_ETA_DET) -> np.ndarray:
+    """Theta_true (M x (bins + 1)) of the loop detector: for i photons bin j
+    clicks with p_j(i) = 1 - (1 - q_j)^i (Eq. pj_fock), bins independently, so
+    the number of clicked bins is Poisson-binomial; computed by the exact
+    recursion over bins (one bin at a time, column-major for speed)."""
+    q = loop_bin_click(bins, R, eta_loop, eta_det)
+    i = np.arange(M, dtype=np.float64)
+    dist = np.zeros((bins + 1, M))
+    dist[0] = 1.0
+    tmp = np.empty(M)
+    for j in range(bins):
+        p = -np.expm1(i * np.log1p(-q[j]))
+        omp = 1.0 - p
+        for n in range(j + 1, 0, -1):
+            np.multiply(dist[n], omp, out=dist[n])
+            np.multiply(dist[n - 1], p, out=tmp)
+            dist[n] += tmp
+        dist[0] *= omp
+    theta = np.ascontiguousarray(dist.T)
+    theta = np.maximum(theta, 0.0)
+    theta /= theta.sum(axis=1, keepdims=True)
+    return theta
+
+
+def config_f2(M: int = F2_M, D: int = F2_D, bins: int = F2_BINS, shots=F2_SHOTS, gamma: float = 1e-5,
+              seed: int = BASE_SEED + 5) -> Workload:
+    """The paper's geometry: loop-detector POVM, probes lambda_d = d^2
+    (d = 0..D-1), multinomial trials per probe, band +-10 sqrt(lambda).
+    Defaults are the paper's sizes; smaller M and D give the same geometry at
+    a smaller scale (D should stay near sqrt(M))."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    theta = loop_detector_povm(M, bins)
+    lam = quadratic_intensities(D)
+    q = outcome_probabilities(lam, theta)
+    P = sample_outcomes(q, shots, rng)
+    return Workload(f"f2_M{M}_N{bins + 1}_D{D}", M, bins + 1, D, lam, P, theta, gamma, 10.0, seed, shots)
