@@ -68,3 +68,14 @@ def test_infidelity_definition():
     np.testing.assert_allclose(oracle.infidelity(C, C[::-1]), 1.0)
     # two-level hand value: (sqrt(.36*.64) + sqrt(.64*.36))^2 = 0.9216
     assert oracle.infidelity(np.array([[0.36], [0.64]]), np.array([[0.64], [0.36]]))[0] == pytest.approx(0.0784)
+
+
+def test_liu_sizes_follow_the_papers_power_laws():
+    """Eq. liu_M / liu_D; the paper quotes N M = 1.04e7 free variables at
+    N = 1000 (the power laws are approximate: within 5 %)."""
+    M, D = workloads.liu_sizes(1000)
+    assert M == round(6.6 * 1000 ** 1.06) and D == round(4.0 * 1000 ** 1.14)
+    assert abs(M * 1000 - 1.04e7) <= 0.05 * 1.04e7
+    w = workloads.config_f3(30, shots=None)
+    assert (w.M, w.D, w.N) == (*workloads.liu_sizes(30), 30)
+    np.testing.assert_allclose(w.theta_true.sum(1), 1.0, atol=1e-13)

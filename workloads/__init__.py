@@ -355,3 +355,23 @@ def config_f2(M: int = F2_M, D: int = F2_D, bins: int = F2_BINS, shots=F2_SHOTS,
     q = outcome_probabilities(lam, theta)
     P = sample_outcomes(q, shots, rng)
     return Workload(f"f2_M{M}_N{bins + 1}_D{D}", M, bins + 1, D, lam, P, theta, gamma, 10.0, seed, shots)
+
+
+# ---- Liu-shaped near-dense geometry (Sec. Application to other detector
+# geometries, Eq. liu_M, Eq. liu_D) --------------------------------------------
+def liu_sizes(N: int) -> tuple[int, int]:
+    """M ~ 6.6 N^1.06 and D ~ 4.0 N^1.14 (rounded)."""
+    return int(round(6.6 * N ** 1.06)), int(round(4.0 * N ** 1.14))
+
+
+def config_f3(N: int, eta: float = 0.9, shots=1_000_000, gamma: float = 1e-4,
+              seed: int | None = None) -> Workload:
+    """Synthetic stand-in for the spatially multiplexed detector of Liu et al.
+    (whose input generator is not available): an equal-split network onto
+    N - 1 click detectors of efficiency eta, outcome n = number of clicking
+    detectors (the uniform-bin chain model of detector_povm), M and D from
+    liu_sizes(N), lambda linear in [0, 0.75 M], multinomial shots.  Seed
+    BASE_SEED + 6 + N unless given."""
+    M, D = liu_sizes(N)
+    return make_workload(f"f3_N{N}_M{M}_D{D}", M, N - 1, eta, D, 0.75 * M, gamma, 10.0, shots,
+                         BASE_SEED + 6 + N if seed is None else seed)
