@@ -143,6 +143,20 @@ static tomo_status stage_in(Plan &p, const double *src, int64_t count, double **
     return TOMO_OK;
 }
 
+// A bounded mbarrier wait of a tensor-core contraction gave up (the kernel
+// set tc_err and stopped its remaining work): report it once and re-arm.
+static tomo_status check_tc_err(Plan &p)
+{
+    if (!hvp_on_tensor_cores(p.precision)) return TOMO_OK;
+    int32_t err = 0;
+    CUDA_TRY(cudaMemcpyAsync(&err, &p.sc->tc_err, sizeof(err), cudaMemcpyDeviceToHost, p.stream));
+    CUDA_TRY(cudaStreamSynchronize(p.stream));
+    if (!err) return TOMO_OK;
+    CUDA_TRY(cudaMemsetAsync(&p.sc->tc_err, 0, sizeof(int32_t), p.stream));
+    CUDA_TRY(cudaStreamSynchronize(p.stream));
+    return fail(TOMO_ETIMEOUT, "a bounded tensor-core pipeline wait gave up");
+}
+
 static tomo_status check_finite(Plan &p, const double *x, int64_t n, const char *what)
 {
     CUDA_TRY(launch_nonfinite_check(p, x, n, 0));
@@ -937,8 +951,7 @@ tomo_status tomo_fit(tomo_plan_t plan, const double *P, double *Theta, const tom
     }
     tomo_status st = fit_impl(p, Pd, o, rep);
     if (st != TOMO_OK) return st;
-    if (p.sc_host->tc_err)
-        return fail(TOMO_ETIMEOUT, "a bounded tensor-core pipeline wait gave up");
+    TOMO_TRY(check_tc_err(p));
     CUDA_TRY(cudaMemcpyAsync(Theta, p.Th, sizeof(double) * size_t(MN),
                              tdev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, p.stream));
     CUDA_TRY(cudaStreamSynchronize(p.stream));
@@ -1011,6 +1024,8 @@ tomo_status tomo_hvp(tomo_plan_t plan, const double *V, double *HV)
     if (!p || !V || !HV) return fail(TOMO_EINVAL, "NULL argument");
     if (hvp_on_tensor_cores(p->precision)) {
         CUDA_TRY(launch_hvp_tc(*p, V, HV, false, false));
+        CUDA_TRY(cudaStreamSynchronize(p->stream));
+        TOMO_TRY(check_tc_err(*p));
     } else {
         CUDA_TRY(launch_forward(*p, prec_products(p->precision), FWD_STORE, V, p->O, nullptr, false));
         CUDA_TRY(launch_adjoint(*p, prec_products(p->precision), ADJ_GRAD, p->O, HV, V, false));
