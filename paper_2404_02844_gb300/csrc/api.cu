@@ -230,12 +230,12 @@ static cudaError_t make_schedule_tc(Plan &p, Schedule &S, const std::vector<int6
     if ((e = dalloc(&S.counters, tiles * ncol))) return e;
     if ((e = dalloc(&S.cta_first, int64_t(cta_first.size())))) return e;
     if ((e = cudaMalloc(&S.part, std::max<int64_t>(1, slots * ncol) * TILE_R * bn * sizeof(float)))) return e;
-    if ((e = cudaMemcpy(S.units, units.data(), sizeof(WorkUnit) * units.size(), cudaMemcpyHostToDevice)) ||
-        (e = cudaMemcpy(S.tile_first, first.data(), sizeof(int32_t) * tiles, cudaMemcpyHostToDevice)) ||
-        (e = cudaMemcpy(S.tile_nsplit, nsplit.data(), sizeof(int32_t) * tiles, cudaMemcpyHostToDevice)) ||
-        (e = cudaMemcpy(S.cta_first, cta_first.data(), sizeof(int32_t) * cta_first.size(),
-                        cudaMemcpyHostToDevice)) ||
-        (e = cudaMemset(S.counters, 0, sizeof(unsigned) * tiles * ncol)))
+    if ((e = cudaMemcpyAsync(S.units, units.data(), sizeof(WorkUnit) * units.size(), cudaMemcpyHostToDevice, p.stream)) ||
+        (e = cudaMemcpyAsync(S.tile_first, first.data(), sizeof(int32_t) * tiles, cudaMemcpyHostToDevice, p.stream)) ||
+        (e = cudaMemcpyAsync(S.tile_nsplit, nsplit.data(), sizeof(int32_t) * tiles, cudaMemcpyHostToDevice, p.stream)) ||
+        (e = cudaMemcpyAsync(S.cta_first, cta_first.data(), sizeof(int32_t) * cta_first.size(),
+                             cudaMemcpyHostToDevice, p.stream)) ||
+        (e = cudaMemsetAsync(S.counters, 0, sizeof(unsigned) * tiles * ncol, p.stream)))
         return e;
     *max_ctas = std::max<int64_t>(*max_ctas, int64_t(S.n_ctas) * ncol);
     return cudaSuccess;
@@ -287,10 +287,10 @@ static cudaError_t make_schedule(Plan &p, Schedule &S, const std::vector<int64_t
     if ((e = dalloc(&S.tile_nsplit, tiles))) return e;
     if ((e = dalloc(&S.counters, tiles * ncol))) return e;
     if ((e = cudaMalloc(&S.part, std::max<int64_t>(1, slots * ncol) * TILE_R * bn * part_elem_bytes))) return e;
-    if ((e = cudaMemcpy(S.units, units.data(), sizeof(WorkUnit) * units.size(), cudaMemcpyHostToDevice)) ||
-        (e = cudaMemcpy(S.tile_first, first.data(), sizeof(int32_t) * tiles, cudaMemcpyHostToDevice)) ||
-        (e = cudaMemcpy(S.tile_nsplit, nsplit.data(), sizeof(int32_t) * tiles, cudaMemcpyHostToDevice)) ||
-        (e = cudaMemset(S.counters, 0, sizeof(unsigned) * tiles * ncol)))
+    if ((e = cudaMemcpyAsync(S.units, units.data(), sizeof(WorkUnit) * units.size(), cudaMemcpyHostToDevice, p.stream)) ||
+        (e = cudaMemcpyAsync(S.tile_first, first.data(), sizeof(int32_t) * tiles, cudaMemcpyHostToDevice, p.stream)) ||
+        (e = cudaMemcpyAsync(S.tile_nsplit, nsplit.data(), sizeof(int32_t) * tiles, cudaMemcpyHostToDevice, p.stream)) ||
+        (e = cudaMemsetAsync(S.counters, 0, sizeof(unsigned) * tiles * ncol, p.stream)))
         return e;
     *max_ctas = std::max<int64_t>(*max_ctas, int64_t(units.size()) * ncol);
     return cudaSuccess;
@@ -304,10 +304,12 @@ static cudaError_t build_schedules(Plan &p, bool tensor_cores)
 {
     std::vector<int32_t> klo(p.fwd_tiles), khi(p.fwd_tiles), dlo(p.adj_tiles), dhi(p.adj_tiles);
     cudaError_t e;
-    if ((e = cudaMemcpy(klo.data(), p.fwd_klo, sizeof(int32_t) * klo.size(), cudaMemcpyDeviceToHost)) ||
-        (e = cudaMemcpy(khi.data(), p.fwd_khi, sizeof(int32_t) * khi.size(), cudaMemcpyDeviceToHost)) ||
-        (e = cudaMemcpy(dlo.data(), p.adj_dlo, sizeof(int32_t) * dlo.size(), cudaMemcpyDeviceToHost)) ||
-        (e = cudaMemcpy(dhi.data(), p.adj_dhi, sizeof(int32_t) * dhi.size(), cudaMemcpyDeviceToHost)))
+    // tile ranges produced by the plan kernels on the plan stream
+    if ((e = cudaMemcpyAsync(klo.data(), p.fwd_klo, sizeof(int32_t) * klo.size(), cudaMemcpyDeviceToHost, p.stream)) ||
+        (e = cudaMemcpyAsync(khi.data(), p.fwd_khi, sizeof(int32_t) * khi.size(), cudaMemcpyDeviceToHost, p.stream)) ||
+        (e = cudaMemcpyAsync(dlo.data(), p.adj_dlo, sizeof(int32_t) * dlo.size(), cudaMemcpyDeviceToHost, p.stream)) ||
+        (e = cudaMemcpyAsync(dhi.data(), p.adj_dhi, sizeof(int32_t) * dhi.size(), cudaMemcpyDeviceToHost, p.stream)) ||
+        (e = cudaStreamSynchronize(p.stream)))
         return e;
     int64_t max_ctas = 0;
     auto ranges = [&](bool fwd, int align_start, int align_end, std::vector<int64_t> &st,
@@ -359,8 +361,8 @@ static cudaError_t build_schedules(Plan &p, bool tensor_cores)
             if ((e = cudaMalloc(&p.ut_hi, ub)) || (e = cudaMalloc(&p.ut_lo, ub)) ||
                 (e = cudaMalloc(&p.ot_hi, ob)) || (e = cudaMalloc(&p.ot_lo, ob)))
                 return e;
-            if ((e = cudaMemset(p.ut_hi, 0, ub)) || (e = cudaMemset(p.ut_lo, 0, ub)) ||
-                (e = cudaMemset(p.ot_hi, 0, ob)) || (e = cudaMemset(p.ot_lo, 0, ob)))
+            if ((e = cudaMemsetAsync(p.ut_hi, 0, ub, p.stream)) || (e = cudaMemsetAsync(p.ut_lo, 0, ub, p.stream)) ||
+                (e = cudaMemsetAsync(p.ot_hi, 0, ob, p.stream)) || (e = cudaMemsetAsync(p.ot_lo, 0, ob, p.stream)))
                 return e;
         }
     }
@@ -625,10 +627,11 @@ tomo_status tomo_plan(tomo_plan_t *out, const tomo_desc *d)
     PLAN_TRY(cudaStreamSynchronize(p->stream));
     PLAN_TRY(build_schedules(*p, hvp_on_tensor_cores(p->precision)));
     PLAN_TRY(dalloc(&p->partials, RED_SLOTS * p->max_partials));
-    if (d->flags & TOMO_PLAN_AUTOTUNE) {
-        PLAN_TRY(autotune(*p));
-        PLAN_TRY(cudaStreamSynchronize(p->stream));
-    }
+    if (d->flags & TOMO_PLAN_AUTOTUNE) PLAN_TRY(autotune(*p));
+    // every initialisation (zeroed counters and operand mirrors) is issued on
+    // the plan stream, which may be non-blocking: finish it before any call
+    // can launch work on another stream
+    PLAN_TRY(cudaStreamSynchronize(p->stream));
 #undef PLAN_TRY
     *out = reinterpret_cast<tomo_plan_t>(p);
     return TOMO_OK;

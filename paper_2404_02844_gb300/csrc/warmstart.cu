@@ -514,9 +514,12 @@ tomo_status tomo_ws_create(tomo_ws_t *out, const tomo_ws_desc *d)
     fill(w->oW2, s.C2 * s.C1 * s.K, double(s.C1 * s.K), 1.0);
     fill(w->oW3, s.H * s.F(), double(s.F()), 1.0);
     fill(w->oW4, s.M * s.C0 * s.H, double(s.H), 0.1);
-    if ((e = cudaMemcpy(w->param, h.data(), sizeof(float) * size_t(o), cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemset(w->m, 0, sizeof(float) * size_t(o))) != cudaSuccess ||
-        (e = cudaMemset(w->v, 0, sizeof(float) * size_t(o))) != cudaSuccess) {
+    // on the handle's stream (possibly non-blocking), finished before return
+    if ((e = cudaMemcpyAsync(w->param, h.data(), sizeof(float) * size_t(o), cudaMemcpyHostToDevice,
+                             w->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(w->m, 0, sizeof(float) * size_t(o), w->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(w->v, 0, sizeof(float) * size_t(o), w->stream)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(w->stream)) != cudaSuccess) {
         free_ws(w);
         return tomo_set_error(TOMO_ECUDA, cudaGetErrorString(e));
     }
