@@ -360,6 +360,9 @@ def main():
             "f_star_status": f_star_status,
             "newton_iters": iters,
             "cg_total": [r["cg_total"] for r in reps],
+            # companion rate: POVM elements times CG Hessian products per second
+            "hvp_rate": {"value": M * N * sum(r["cg_total"] for r in reps) * world / T,
+                         "unit": "POVM-elem*HVPs/s"},
             "stop": reps[-1]["stop_name"],
             "plain_fp64": plain,
             "roofline": roofline,
