@@ -152,7 +152,13 @@ static tomo_status check_tc_err(Plan &p)
     CUDA_TRY(cudaMemcpyAsync(&err, &p.sc->tc_err, sizeof(err), cudaMemcpyDeviceToHost, p.stream));
     CUDA_TRY(cudaStreamSynchronize(p.stream));
     if (!err) return TOMO_OK;
+    // a CTA that gave up skipped its remaining units: the split-K counters
+    // and the fused-restriction ticket may be left mid-count, so re-arm them
     CUDA_TRY(cudaMemsetAsync(&p.sc->tc_err, 0, sizeof(int32_t), p.stream));
+    CUDA_TRY(cudaMemsetAsync(&p.sc->ticket[1], 0, sizeof(unsigned int), p.stream));
+    const int64_t ncol = (p.N + band_bn(p.N) - 1) / band_bn(p.N);
+    CUDA_TRY(cudaMemsetAsync(p.sched_tc[0].counters, 0, sizeof(unsigned) * size_t(p.fwd_tiles * ncol), p.stream));
+    CUDA_TRY(cudaMemsetAsync(p.sched_tc[1].counters, 0, sizeof(unsigned) * size_t(p.adj_tiles * ncol), p.stream));
     CUDA_TRY(cudaStreamSynchronize(p.stream));
     return fail(TOMO_ETIMEOUT, "a bounded tensor-core pipeline wait gave up");
 }
