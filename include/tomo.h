@@ -224,6 +224,14 @@ typedef struct {
 
 tomo_status tomo_plan_info(tomo_plan_t plan, tomo_plan_info_t *info);
 
+/* Self-test of the bounded device waits (no counterpart in the paper): runs
+ * one tensor-core Hessian product whose tensor-core instructions are
+ * withheld and whose mbarrier waits are bounded at 4096 polls, so every wait
+ * gives up; the kernels flag it and return without faulting.  Returns what
+ * a real timeout returns, TOMO_ETIMEOUT, after re-arming the plan (it stays
+ * usable).  EINVAL for a plan not in the tensor-core form. */
+tomo_status tomo_selftest_tc_timeout(tomo_plan_t plan);
+
 /* Hessian diagonal h_i = 2 sum_d F_{d,i}^2 + 2 gamma L_ii (Table ops), M
  * doubles, always computed in double at plan time. */
 tomo_status tomo_hess_diag(tomo_plan_t plan, double *h);

@@ -89,6 +89,7 @@ EXPORTS = [
     ("tomo_hvp", c_i32, [c_ptr, c_ptr, c_ptr]),
     ("tomo_hess_diag", c_i32, [c_ptr, c_ptr]),
     ("tomo_plan_info", c_i32, [c_ptr, ctypes.POINTER(tomo_plan_info_t)]),
+    ("tomo_selftest_tc_timeout", c_i32, [c_ptr]),
     ("tomo_project_simplex", c_i32, [c_ptr, c_ptr, c_ptr]),
     ("tomo_smooth", c_i32, [c_ptr, c_ptr, c_ptr, c_i64, c_dbl]),
     ("tomo_infidelity", c_i32, [c_ptr, c_ptr, c_ptr, c_ptr]),

@@ -1061,6 +1061,17 @@ tomo_status tomo_plan_info(tomo_plan_t plan, tomo_plan_info_t *info)
     return TOMO_OK;
 }
 
+tomo_status tomo_selftest_tc_timeout(tomo_plan_t plan)
+{
+    Plan *p = reinterpret_cast<Plan *>(plan);
+    if (!p) return fail(TOMO_EINVAL, "NULL argument");
+    if (!hvp_on_tensor_cores(p->precision)) return fail(TOMO_EINVAL, "the plan is not in the tensor-core form");
+    CUDA_TRY(launch_fill(*p, p->p, 1.0 / double(p->N), p->M * p->N));
+    CUDA_TRY(launch_hvp_tc_wait_selftest(*p, p->p, p->q));
+    CUDA_TRY(cudaStreamSynchronize(p->stream));
+    return check_tc_err(*p);
+}
+
 tomo_status tomo_hess_diag(tomo_plan_t plan, double *h)
 {
     Plan *p = reinterpret_cast<Plan *>(plan);

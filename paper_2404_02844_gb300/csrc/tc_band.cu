@@ -97,6 +97,10 @@ struct TcArgs {
     unsigned int *pq_ticket;
     DevScalars *sc;
     int n_tiles;
+    // bound of every mbarrier wait (polls); the wait self-test withholds the
+    // MMAs (skip_mma) so that every wait runs to this bound and gives up
+    uint32_t wait_limit;
+    int skip_mma;
 };
 
 // Float weights of the run of 8 photon numbers i_r.. of probe d (zero outside
@@ -340,7 +344,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(TcArgs a)
             // the MMAs of step g - 2 (maybe of the previous unit) read this A
             // stage and the B stage of step g + 1; their completion also
             // covers every earlier step
-            if (!tc::mbar_wait_bounded(&bars[st], ((g / TC_STAGES) - 1) & 1u, TC_WAIT_LIMIT))
+            if (!tc::mbar_wait_bounded(&bars[st], ((g / TC_STAGES) - 1) & 1u, a.wait_limit))
                 ok = false;
         }
         const int64_t k0 = int64_t(wu.k0) + int64_t(s) * TC_BK;
@@ -396,7 +400,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(TcArgs a)
         tc::fence_proxy_async_smem();
         tc::tc_fence_before_sync();
         __syncthreads();
-        if (tid == 0) {
+        if (tid == 0 && !a.skip_mma) {
             tc::tc_fence_after_sync();
             const uint32_t a_hi = tc::smem_u32(A_hi), a_lo = tc::smem_u32(A_lo);
             const uint32_t b_hi = tc::smem_u32(B_hi), b_lo = tc::smem_u32(B_lo);
@@ -415,7 +419,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(TcArgs a)
     }
     if (nsteps > 0) {
         const uint32_t g = gstep + uint32_t(nsteps - 1);
-        if (!tc::mbar_wait_bounded(&bars[g % TC_STAGES], (g / TC_STAGES) & 1u, TC_WAIT_LIMIT))
+        if (!tc::mbar_wait_bounded(&bars[g % TC_STAGES], (g / TC_STAGES) & 1u, a.wait_limit))
             ok = false;
     }
     gstep += uint32_t(nsteps);
@@ -841,6 +845,8 @@ static TcArgs tc_args(Plan &p, bool fwd, const int32_t *gate)
     a.pq_ticket = &p.sc->ticket[1];
     a.sc = p.sc;
     a.n_tiles = p.adj_tiles;
+    a.wait_limit = TC_WAIT_LIMIT;
+    a.skip_mma = 0;
     return a;
 }
 
@@ -872,6 +878,30 @@ cudaError_t launch_hvp_tc(Plan &p, const void *V, void *HV, bool vec_f32, bool g
     b.u = V;
     b.vec_f32 = vec_f32 ? 1 : 0;
     b.restrict_stage = (vec_f32 && tc_restrict_fusable(p)) ? restrict_stage : 0;
+    return launch_tc<false>(p, b);
+}
+
+// Self-test of the bounded waits: one Hessian product (double vectors) whose
+// MMAs are withheld, so no mbarrier ever completes; with waits bounded at 4096
+// polls every CTA gives up after its first unit, sets the error flag and
+// returns.  Nothing is left in flight (no MMA was issued, every copy is waited
+// for), so the context stays usable; the host re-arms the counters.
+cudaError_t launch_hvp_tc_wait_selftest(Plan &p, const double *V, double *HV)
+{
+    dim3 tb(32, 8), tg(unsigned((p.M + 31) / 32), unsigned((p.N + 31) / 32));
+    k_transpose_split<double><<<tg, tb, 0, p.stream>>>(nullptr, p.M, p.N, V, p.ut_hi, p.ut_lo, p.ut_pitch);
+    count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    TcArgs f = tc_args(p, true, nullptr);
+    f.wait_limit = 4096;
+    f.skip_mma = 1;
+    if ((e = launch_tc<true>(p, f)) != cudaSuccess) return e;
+    TcArgs b = tc_args(p, false, nullptr);
+    b.q = HV;
+    b.u = V;
+    b.wait_limit = 4096;
+    b.skip_mma = 1;
     return launch_tc<false>(p, b);
 }
 

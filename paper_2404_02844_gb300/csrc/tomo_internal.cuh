@@ -188,6 +188,7 @@ inline bool hvp_on_tensor_cores(int precision) { return precision == TOMO_PREC_T
 // and finishes p^T q and alpha (float vectors, when tc_restrict_fusable)
 cudaError_t launch_hvp_tc(Plan &p, const void *V, void *HV, bool vec_f32, bool gated, int restrict_stage = 0);
 bool tc_restrict_fusable(const Plan &p);
+cudaError_t launch_hvp_tc_wait_selftest(Plan &p, const double *V, double *HV);
 size_t tc_smem_bytes(int bn);
 
 // records a failure message for tomo_last_error (api.cu)

@@ -424,3 +424,24 @@ def test_autotuned_plan_keeps_the_solution_and_caches_its_choice(tomo, prec):
     with tomo.Plan.from_workload(w, precision=prec, autotune=True) as again:
         info2 = again.info()
     assert info2["from_cache"] == 1 and info2["density"] == info["density"]
+
+
+def test_bounded_tensor_core_waits_report_a_timeout_and_leave_the_plan_usable(tomo):
+    """Failure detection without a GPU fault: the self-test withholds the
+    tensor-core instructions so that every bounded mbarrier wait gives up; the
+    host must see TOMO_ETIMEOUT, and the plan must give the same Hessian
+    product and fit afterwards as before."""
+    w = workloads.small_case(M=300, bins=15, D=400, X=250.0, gamma=1e-2, seed=78)
+    rng = np.random.default_rng(5)
+    X = dev(rng.random((w.M, w.N)))
+    with tomo.Plan.from_workload(w, precision="tc") as pl:
+        hv0 = pl.hvp(X)
+        st = tomo.lib().tomo_selftest_tc_timeout(pl._h)
+        assert st == 5, (st, tomo.tomo_last_error())            # TOMO_ETIMEOUT
+        assert "gave up" in tomo.tomo_last_error()
+        hv1 = pl.hvp(X)
+        assert torch.equal(hv0, hv1)
+        Th, rep = pl.fit(dev(w.P), eps_kkt=1e-10, max_newton=600)
+        assert rep["status"] == "TOMO_OK", rep
+    with tomo.Plan.from_workload(w, precision="fp32") as pl:
+        assert tomo.lib().tomo_selftest_tc_timeout(pl._h) == 1   # EINVAL: not the tensor-core form
