@@ -154,14 +154,17 @@ def checks(L):
             failed.append("solve")
         if not (abs(oracle.poisson(7, 3.5) - poisson.pmf(7, 3.5)) <= 1e-13 * poisson.pmf(7, 3.5)):
             failed.append("poisson")
-        # Armijo (App. B): every accepted step decreases f (c1, first 30
-        # iterations; CG capped at 50 products so that full steps overshoot
-        # and the rule has to reject some trials)
-        w = workloads.config_c1()
-        pc = oracle.Problem.from_workload(w)
-        _, _, hc = pc.fit(w.P, max_newton=30, eps_kkt=0.0, max_cg=50)
-        if not np.all(np.diff(hc) <= 0.0):
-            failed.append("monotone")
+        # Armijo (App. B): every accepted step decreases f beyond rounding
+        # (two small cases, 40 iterations with CG capped at 10 products so
+        # that full steps overshoot and the rule has to reject trials; a
+        # relative rise above 1e-12 is a rule violation, below it rounding)
+        for w in (workloads.small_case(seed=101),
+                  workloads.small_case(M=40, bins=5, D=60, X=30.0, seed=102)):
+            pc = oracle.Problem.from_workload(w)
+            _, _, hc = pc.fit(w.P, max_newton=40, eps_kkt=0.0, max_cg=10)
+            if np.max(np.diff(hc) / hc[:-1]) > 1e-12:
+                failed.append("monotone")
+                break
     finally:
         oracle._lib = saved
     return failed
