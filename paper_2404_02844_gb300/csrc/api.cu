@@ -224,9 +224,9 @@ static cudaError_t make_schedule_tc(Plan &p, Schedule &S, const std::vector<int6
         units.insert(units.end(), v.begin(), v.end());
         cta_first.push_back(int32_t(units.size()));
     }
+    // every unit writes a partial tile (the finish kernel combines them)
     int64_t slots = 0;
-    for (int t = 0; t < tiles; ++t)
-        if (nsplit[t] > 1) { first[t] = int32_t(slots); slots += nsplit[t]; }
+    for (int t = 0; t < tiles; ++t) { first[t] = int32_t(slots); slots += nsplit[t]; }
     cudaError_t e;
     S.n_units = int(units.size());
     S.n_ctas = int(cta_first.size()) - 1;
@@ -243,7 +243,8 @@ static cudaError_t make_schedule_tc(Plan &p, Schedule &S, const std::vector<int6
                              cudaMemcpyHostToDevice, p.stream)) ||
         (e = cudaMemsetAsync(S.counters, 0, sizeof(unsigned) * tiles * ncol, p.stream)))
         return e;
-    *max_ctas = std::max<int64_t>(*max_ctas, int64_t(S.n_ctas) * ncol);
+    // the finish kernel's grid reduction: one partial per (32-row slice, column block)
+    *max_ctas = std::max<int64_t>(*max_ctas, std::max<int64_t>(S.n_ctas, tiles * (TILE_R / 32)) * ncol);
     return cudaSuccess;
 }
 

@@ -84,19 +84,18 @@ struct TcArgs {
     const void *u;
     int vec_f32;
     double gamma;
-    // CG restriction fused into the adjoint epilogue (float vectors, one
+    // CG restriction fused into the adjoint finish (float vectors, one
     // column block, N % 4 == 0): q <- q - q_{i,m(i)} (stage 2) on the free
-    // variables, 0 elsewhere, and p^T q; each tile's owner writes its partial
-    // dot and the last tile sums them in tile order and sets alpha = rz / pq
-    // (or stops the CG on non-positive curvature)
+    // variables, 0 elsewhere, and p^T q, reduced over the finish CTAs in a
+    // fixed order; the last CTA sets alpha = rz / pq (or stops the CG on
+    // non-positive curvature)
     int restrict_stage;           // 0: off, 1 or 2: the CG stage
     const uint8_t *freem;
     const int32_t *mrow;
     const float *pvec;
-    double *pq_part;              // one per adjoint tile
-    unsigned int *pq_ticket;
+    double *red_part;             // grid-reduction partials (one per finish CTA)
+    int64_t red_stride;
     DevScalars *sc;
-    int n_tiles;
     // bound of every mbarrier wait (polls); the wait self-test withholds the
     // MMAs (skip_mma) so that every wait runs to this bound and gives up
     uint32_t wait_limit;
@@ -256,7 +255,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(TcArgs a)
     // pipeline steps issued by this CTA so far (stage and mbarrier phase of
     // every step follow from it across units)
     uint32_t gstep = 0;
-    __shared__ int last;
 
     // the CTA's units, in order (one wave of persistent CTAs)
     const int u_end = a.cta_first[blockIdx.x + 1];
@@ -425,23 +423,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(TcArgs a)
     gstep += uint32_t(nsteps);
     tc::tc_fence_after_sync();
 
-    // ---- epilogue, through a shared-memory copy of the tile ----
-    // (the stage buffers: every MMA and copy of this unit is complete).  Warp
-    // w reads TMEM lanes 32 (w % 4) .. + 31 (tile rows) and the column half
-    // w / 4 (BN >= 64) or all columns (BN == 32, warps 0-3 only); every
-    // global access below runs along rows (split-K partials, the adjoint's
-    // u and q) or along the transposed rows (the forward's O^T copies).
+    // ---- this unit's f32 partial tile (split-K) ----
+    // through a shared-memory copy (the stage buffers: every MMA and copy of
+    // this unit is complete) so that the global writes run along rows.  The
+    // finish kernel sums the partials of every tile in unit order and runs
+    // the epilogue, spread over many CTAs.  Warp w reads TMEM lanes
+    // 32 (w % 4) .. + 31 (tile rows) and the column half w / 4 (BN >= 64) or
+    // all columns (BN == 32, warps 0-3 only).
     const int lg = warp & 3;
     const int row = lg * 32 + lane;
     constexpr int COLS_PER_WARP = BN >= 64 ? BN / 2 : BN;
     const int col0 = BN >= 64 ? (warp >> 2) * COLS_PER_WARP : 0;
     const bool active = BN >= 64 || warp < 4;
-    const int nsplit = a.tile_nsplit[tile];
     const int ncb = gridDim.y;
     constexpr int LD = BN + 1;                 // padded row: conflict-free both ways
     constexpr int TE = TILE_R * BN;
     float *tile_s = reinterpret_cast<float *>(sm);
-
     if (active) {
 #pragma unroll
         for (int c = 0; c < COLS_PER_WARP; c += 32) {
@@ -457,299 +454,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(TcArgs a)
         }
     }
     __syncthreads();
-    bool owner = true;
-    if (nsplit > 1) {
-        // this unit's partial tile, then the split-K ticket: the unit that
-        // completes the tile sums every partial in unit order (deterministic)
-        const int64_t split_stride = int64_t(ncb) * TE;
-        const float *base = a.part + (int64_t(a.tile_first[tile]) * ncb + blockIdx.y) * TE;
+    {
         float *mine = a.part + (int64_t(a.tile_first[tile] + wu.chunk) * ncb + blockIdx.y) * TE;
         for (int e = tid; e < TE; e += TC_THREADS) mine[e] = tile_s[(e / BN) * LD + (e % BN)];
-        __threadfence();
-        __syncthreads();
-        if (tid == 0) {
-            unsigned *ctr = &a.counters[int64_t(tile) * ncb + blockIdx.y];
-            last = atomicAdd(ctr, 1u) == unsigned(nsplit - 1);
-            if (last) *ctr = 0u;
-        }
-        __syncthreads();
-        owner = last != 0;
-        if (owner) {
-            __threadfence();
-            // each thread sums P4 float4 columns of the tile over the splits,
-            // split by split (P4 independent loads in flight per thread)
-            // the splits' loads are software-pipelined (the next split's loads
-            // are in flight while the current one is added), in halves of at
-            // most 8 float4 per thread to bound the registers
-            constexpr int P4 = TE / 4 / TC_THREADS;
-            constexpr int PH = P4 < 8 ? P4 : 8;
-            static_assert(TE % (4 * TC_THREADS) == 0 && P4 % PH == 0, "tile divides into float4 per thread");
-#pragma unroll 1
-            for (int h0 = 0; h0 < P4; h0 += PH) {
-                float4 acc4[PH], cur[PH];
-#pragma unroll
-                for (int j = 0; j < PH; ++j) {
-                    acc4[j] = make_float4(0.f, 0.f, 0.f, 0.f);
-                    cur[j] = __ldcg(reinterpret_cast<const float4 *>(base) + tid + (h0 + j) * TC_THREADS);
-                }
-                for (int sidx = 0; sidx < nsplit; ++sidx) {
-                    float4 nxt[PH];
-                    if (sidx + 1 < nsplit) {
-                        const float4 *src = reinterpret_cast<const float4 *>(base + (sidx + 1) * split_stride);
-#pragma unroll
-                        for (int j = 0; j < PH; ++j) nxt[j] = __ldcg(src + tid + (h0 + j) * TC_THREADS);
-                    }
-#pragma unroll
-                    for (int j = 0; j < PH; ++j) {
-                        acc4[j].x += cur[j].x; acc4[j].y += cur[j].y; acc4[j].z += cur[j].z; acc4[j].w += cur[j].w;
-                    }
-                    if (sidx + 1 < nsplit) {
-#pragma unroll
-                        for (int j = 0; j < PH; ++j) cur[j] = nxt[j];
-                    }
-                }
-#pragma unroll
-                for (int j = 0; j < PH; ++j) {
-                    const int e = (tid + (h0 + j) * TC_THREADS) * 4, rr = e / BN, cc = e % BN;
-                    float *d = &tile_s[rr * LD + cc];
-                    d[0] = acc4[j].x; d[1] = acc4[j].y; d[2] = acc4[j].z; d[3] = acc4[j].w;
-                }
-            }
-            __syncthreads();
-        }
-    }
-    if (FWD && owner) {
-        // O^T hi/lo copies for the adjoint's operand B: consecutive threads
-        // take consecutive pairs of probes of one outcome column (one 4-byte
-        // store per part; the row offset r0 and the pitch are even)
-        for (int e = tid; e < TE / 2; e += TC_THREADS) {
-            const int nl = e / (TILE_R / 2), rr = (e % (TILE_R / 2)) * 2;
-            const int64_t grow = r0 + rr, n = n0 + nl;
-            if (grow >= a.D || n >= a.N) continue;
-            const float v0 = tile_s[rr * LD + nl];
-            const float v1 = grow + 1 < a.D ? tile_s[(rr + 1) * LD + nl] : 0.f;
-            const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
-            const float2 hf = __bfloat1622float2(h);
-            const __nv_bfloat162 l = __floats2bfloat162_rn(v0 - hf.x, v1 - hf.y);
-            if (grow + 1 < a.D) {
-                *reinterpret_cast<__nv_bfloat162 *>(a.o_hi + n * a.opitch + grow) = h;
-                *reinterpret_cast<__nv_bfloat162 *>(a.o_lo + n * a.opitch + grow) = l;
-            } else {
-                a.o_hi[n * a.opitch + grow] = h.x;
-                a.o_lo[n * a.opitch + grow] = l.x;
-            }
-        }
-    }
-    if (!FWD && owner && a.vec_f32 && (a.N % 4) == 0) {
-        // q = 2 Z + 2 gamma L u, float vectors: a thread takes 4 consecutive
-        // columns (float4) of TILE_R / RPI rows, and the loads of UNR rows
-        // are all issued before any of them is used (memory-level
-        // parallelism: this epilogue runs once per tile, on the critical path)
-        constexpr int CG = BN / 4;                 // float4 column groups per row
-        constexpr int RPI = TC_THREADS / CG;       // rows per pass
-        constexpr int PASSES = TILE_R / RPI;
-        constexpr int UNR = 4;
-        static_assert(PASSES % UNR == 0, "passes divide by the unroll");
-        const float g2f = float(2.0 * a.gamma);
-        const float *u = static_cast<const float *>(a.u);
-        float *q = static_cast<float *>(a.q);
-        const int cc = (tid % CG) * 4;
-        const int64_t n = n0 + cc;
-        const int rstage = a.restrict_stage;
-        float *qm_s = tile_s + TILE_R * LD;        // per-row q_{i,m(i)} (stage 2)
-        if (rstage != 0) {
-            if (tid < TILE_R) {
-                const int64_t grow = r0 + tid;
-                float qm = 0.f;
-                if (rstage == 2 && grow < a.M) {
-                    const int m = a.mrow[grow];
-                    float lx = 0.f;
-                    if (g2f != 0.f) {
-                        const float xc = u[grow * a.N + m];
-                        if (grow < a.M - 1) lx += xc - u[(grow + 1) * a.N + m];
-                        if (grow > 0) lx += xc - u[(grow - 1) * a.N + m];
-                    }
-                    qm = fmaf(g2f, lx, 2.f * tile_s[tid * LD + (m - int(n0))]);
-                }
-                qm_s[tid] = qm;
-            }
-            __syncthreads();
-        }
-        float pq_acc = 0.f;
-        for (int p0 = 0; p0 < PASSES; p0 += UNR) {
-            float4 uc[UNR], ud[UNR], uu[UNR], pv[UNR];
-            uchar4 fm[UNR];
-#pragma unroll
-            for (int j = 0; j < UNR; ++j) {
-                const int rr = (p0 + j) * RPI + tid / CG;
-                const int64_t grow = r0 + rr;
-                const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-                uc[j] = ud[j] = uu[j] = pv[j] = z4;
-                fm[j] = make_uchar4(0, 0, 0, 0);
-                if (rstage != 0 && grow < a.M && n < a.N) {
-                    fm[j] = *reinterpret_cast<const uchar4 *>(a.freem + grow * a.N + n);
-                    pv[j] = *reinterpret_cast<const float4 *>(a.pvec + grow * a.N + n);
-                }
-                if (grow < a.M && n < a.N && g2f != 0.f) {
-                    const float4 *row = reinterpret_cast<const float4 *>(u + grow * a.N + n);
-                    uc[j] = *row;
-                    if (grow < a.M - 1) ud[j] = *reinterpret_cast<const float4 *>(u + (grow + 1) * a.N + n);
-                    if (grow > 0) uu[j] = *reinterpret_cast<const float4 *>(u + (grow - 1) * a.N + n);
-                }
-            }
-#pragma unroll
-            for (int j = 0; j < UNR; ++j) {
-                const int rr = (p0 + j) * RPI + tid / CG;
-                const int64_t grow = r0 + rr;
-                if (grow >= a.M || n >= a.N) continue;
-                const bool has_d = grow < a.M - 1, has_u = grow > 0;
-                const float *zr = &tile_s[rr * LD + cc];
-                float4 o;
-                o.x = fmaf(g2f, (has_d ? uc[j].x - ud[j].x : 0.f) + (has_u ? uc[j].x - uu[j].x : 0.f), 2.f * zr[0]);
-                o.y = fmaf(g2f, (has_d ? uc[j].y - ud[j].y : 0.f) + (has_u ? uc[j].y - uu[j].y : 0.f), 2.f * zr[1]);
-                o.z = fmaf(g2f, (has_d ? uc[j].z - ud[j].z : 0.f) + (has_u ? uc[j].z - uu[j].z : 0.f), 2.f * zr[2]);
-                o.w = fmaf(g2f, (has_d ? uc[j].w - ud[j].w : 0.f) + (has_u ? uc[j].w - uu[j].w : 0.f), 2.f * zr[3]);
-                if (rstage != 0) {
-                    const float qm = qm_s[rr];
-                    o.x = fm[j].x ? o.x - qm : 0.f;
-                    o.y = fm[j].y ? o.y - qm : 0.f;
-                    o.z = fm[j].z ? o.z - qm : 0.f;
-                    o.w = fm[j].w ? o.w - qm : 0.f;
-                    pq_acc = fmaf(pv[j].x, o.x, pq_acc);
-                    pq_acc = fmaf(pv[j].y, o.y, pq_acc);
-                    pq_acc = fmaf(pv[j].z, o.z, pq_acc);
-                    pq_acc = fmaf(pv[j].w, o.w, pq_acc);
-                }
-                *reinterpret_cast<float4 *>(q + grow * a.N + n) = o;
-            }
-        }
-        if (rstage != 0) {
-            // the tile's partial p^T q (double across threads, fixed tree),
-            // then the last tile's owner finishes the dot in tile order
-            __shared__ double red_s[TC_THREADS / 32];
-            __shared__ int last_tile;
-            double v = double(pq_acc);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0) red_s[warp] = v;
-            __syncthreads();
-            if (tid == 0) {
-                double t = 0.0;
-                for (int w = 0; w < TC_THREADS / 32; ++w) t += red_s[w];
-                a.pq_part[tile] = t;
-                __threadfence();
-                last_tile = atomicAdd(a.pq_ticket, 1u) == unsigned(a.n_tiles - 1);
-            }
-            __syncthreads();
-            if (last_tile) {
-                __threadfence();
-                double t = 0.0;
-                for (int k = tid; k < a.n_tiles; k += TC_THREADS) t += __ldcg(&a.pq_part[k]);
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-                __syncthreads();
-                if (lane == 0) red_s[warp] = t;
-                __syncthreads();
-                if (tid == 0) {
-                    double pq = 0.0;
-                    for (int w = 0; w < TC_THREADS / 32; ++w) pq += red_s[w];
-                    DevScalars *sc = a.sc;
-                    sc->pq = pq;
-                    if (!(pq > 0.0)) sc->cg_active = 0;
-                    else sc->alpha = sc->rz / pq;
-                    *a.pq_ticket = 0u;
-                    __threadfence();
-                }
-            }
-        }
-    } else if (!FWD && owner && !a.vec_f32 && (a.N % 4) == 0) {
-        // the same for double vectors (two double2 per 4 columns)
-        constexpr int CG = BN / 4;
-        constexpr int RPI = TC_THREADS / CG;
-        constexpr int PASSES = TILE_R / RPI;
-        constexpr int UNR = 4;
-        const double g2 = 2.0 * a.gamma;
-        const double *u = static_cast<const double *>(a.u);
-        double *q = static_cast<double *>(a.q);
-        const int cc = (tid % CG) * 4;
-        const int64_t n = n0 + cc;
-        for (int p0 = 0; p0 < PASSES; p0 += UNR) {
-            double2 uc[UNR][2], ud[UNR][2], uu[UNR][2];
-#pragma unroll
-            for (int j = 0; j < UNR; ++j) {
-                const int rr = (p0 + j) * RPI + tid / CG;
-                const int64_t grow = r0 + rr;
-#pragma unroll
-                for (int h = 0; h < 2; ++h) uc[j][h] = ud[j][h] = uu[j][h] = make_double2(0.0, 0.0);
-                if (grow < a.M && n < a.N && g2 != 0.0) {
-                    const double2 *c0 = reinterpret_cast<const double2 *>(u + grow * a.N + n);
-                    uc[j][0] = c0[0];
-                    uc[j][1] = c0[1];
-                    if (grow < a.M - 1) {
-                        const double2 *d0 = reinterpret_cast<const double2 *>(u + (grow + 1) * a.N + n);
-                        ud[j][0] = d0[0];
-                        ud[j][1] = d0[1];
-                    }
-                    if (grow > 0) {
-                        const double2 *u0 = reinterpret_cast<const double2 *>(u + (grow - 1) * a.N + n);
-                        uu[j][0] = u0[0];
-                        uu[j][1] = u0[1];
-                    }
-                }
-            }
-#pragma unroll
-            for (int j = 0; j < UNR; ++j) {
-                const int rr = (p0 + j) * RPI + tid / CG;
-                const int64_t grow = r0 + rr;
-                if (grow >= a.M || n >= a.N) continue;
-                const bool has_d = grow < a.M - 1, has_u = grow > 0;
-                const float *zr = &tile_s[rr * LD + cc];
-                double out[4];
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    const double xc = c & 1 ? uc[j][c >> 1].y : uc[j][c >> 1].x;
-                    const double xd = c & 1 ? ud[j][c >> 1].y : ud[j][c >> 1].x;
-                    const double xu = c & 1 ? uu[j][c >> 1].y : uu[j][c >> 1].x;
-                    double lx = 0.0;
-                    if (has_d) lx += xc - xd;
-                    if (has_u) lx += xc - xu;
-                    out[c] = 2.0 * double(zr[c]) + g2 * lx;
-                }
-                double2 *qo = reinterpret_cast<double2 *>(q + grow * a.N + n);
-                qo[0] = make_double2(out[0], out[1]);
-                qo[1] = make_double2(out[2], out[3]);
-            }
-        }
-    } else if (!FWD && owner) {
-        // q = 2 Z + 2 gamma L u along rows (N not a multiple of 4)
-        const double g2 = 2.0 * a.gamma;
-        const float g2f = float(g2);
-        for (int e = tid; e < TE; e += TC_THREADS) {
-            const int rr = e / BN, cc = e - (e / BN) * BN;
-            const int64_t grow = r0 + rr, n = n0 + cc;
-            if (grow >= a.M || n >= a.N) continue;
-            const int64_t k = grow * a.N + n;
-            const float z = tile_s[rr * LD + cc];
-            if (a.vec_f32) {
-                const float *u = static_cast<const float *>(a.u);
-                float lx = 0.f;
-                if (g2f != 0.f) {
-                    const float xi = u[k];
-                    if (grow < a.M - 1) lx += xi - u[k + a.N];
-                    if (grow > 0) lx += xi - u[k - a.N];
-                }
-                static_cast<float *>(a.q)[k] = fmaf(g2f, lx, 2.f * z);
-            } else {
-                const double *u = static_cast<const double *>(a.u);
-                double lx = 0.0;
-                if (g2 != 0.0) {
-                    const double xi = u[k];
-                    if (grow < a.M - 1) lx += xi - u[k + a.N];
-                    if (grow > 0) lx += xi - u[k - a.N];
-                }
-                static_cast<double *>(a.q)[k] = 2.0 * double(z) + g2 * lx;
-            }
-        }
     }
     // the next unit's first MMA overwrites the accumulator and its tables
     // replace these: every thread is past its tensor-memory loads.  A wait
@@ -762,6 +469,211 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(TcArgs a)
     }  // units
     if (warp == 0) tc::tmem_dealloc(tmem, L::TMEM_COLS);
     if (!ok && tid == 0) atomicExch(a.err, 1);
+}
+
+
+// ----------------------------------------------------------------------------
+// Finish of a tensor-core contraction: one CTA per (32-row slice of a tile,
+// column block) sums the tile's split-K partials in unit order (loads of the
+// next split in flight while the current one is added) and runs the epilogue
+// of its slice:
+//   forward:  the transposed bf16 hi/lo copies of O = F u (the adjoint's B
+//             operand), stored as pairs along the probes;
+//   adjoint:  q = 2 Z + 2 gamma L u along rows, with the optional CG
+//             restriction and the p^T q grid reduction.
+// ----------------------------------------------------------------------------
+constexpr int FIN_RB = 32;            // rows per finish CTA
+constexpr int FIN_T = 256;
+
+template <int BN, bool FWD>
+__global__ void __launch_bounds__(FIN_T) k_tc_finish(TcArgs a)
+{
+    if (a.gate && *a.gate == 0) return;
+    constexpr int LD = BN + 1;
+    constexpr int TE = TILE_R * BN;
+    constexpr int IE = FIN_RB * BN;
+    constexpr int P4 = IE / 4 / FIN_T;
+    static_assert(IE % (4 * FIN_T) == 0, "slice divides into float4 per thread");
+    __shared__ float zs[FIN_RB * LD];
+    __shared__ float qm_s[FIN_RB];
+    const int tid = threadIdx.x, lane = tid & 31;
+    constexpr int SLICES = TILE_R / FIN_RB;
+    const int tile = blockIdx.x / SLICES, rq = blockIdx.x % SLICES;
+    const int64_t r0 = int64_t(tile) * TILE_R + int64_t(rq) * FIN_RB;
+    const int64_t n0 = int64_t(blockIdx.y) * BN;
+    const int ncb = gridDim.y;
+    const int nsplit = a.tile_nsplit[tile];
+    const int64_t split_stride = int64_t(ncb) * TE;
+    const float4 *base = reinterpret_cast<const float4 *>(
+        a.part + (int64_t(a.tile_first[tile]) * ncb + blockIdx.y) * TE + int64_t(rq) * IE);
+
+    float4 acc[P4], cur[P4];
+#pragma unroll
+    for (int j = 0; j < P4; ++j) {
+        acc[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+        cur[j] = __ldcg(base + tid + j * FIN_T);
+    }
+    for (int sidx = 0; sidx < nsplit; ++sidx) {
+        float4 nxt[P4];
+        if (sidx + 1 < nsplit) {
+            const float4 *src = base + (sidx + 1) * (split_stride / 4);
+#pragma unroll
+            for (int j = 0; j < P4; ++j) nxt[j] = __ldcg(src + tid + j * FIN_T);
+        }
+#pragma unroll
+        for (int j = 0; j < P4; ++j) {
+            acc[j].x += cur[j].x; acc[j].y += cur[j].y; acc[j].z += cur[j].z; acc[j].w += cur[j].w;
+        }
+        if (sidx + 1 < nsplit) {
+#pragma unroll
+            for (int j = 0; j < P4; ++j) cur[j] = nxt[j];
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < P4; ++j) {
+        const int e = (tid + j * FIN_T) * 4, rr = e / BN, cc = e % BN;
+        float *d = &zs[rr * LD + cc];
+        d[0] = acc[j].x; d[1] = acc[j].y; d[2] = acc[j].z; d[3] = acc[j].w;
+    }
+    __syncthreads();
+
+    if (FWD) {
+        for (int e = tid; e < IE / 2; e += FIN_T) {
+            const int nl = e / (FIN_RB / 2), rr = (e % (FIN_RB / 2)) * 2;
+            const int64_t grow = r0 + rr, n = n0 + nl;
+            if (grow >= a.D || n >= a.N) continue;
+            const float v0 = zs[rr * LD + nl];
+            const float v1 = grow + 1 < a.D ? zs[(rr + 1) * LD + nl] : 0.f;
+            const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+            const float2 hf = __bfloat1622float2(h);
+            const __nv_bfloat162 l = __floats2bfloat162_rn(v0 - hf.x, v1 - hf.y);
+            if (grow + 1 < a.D) {
+                *reinterpret_cast<__nv_bfloat162 *>(a.o_hi + n * a.opitch + grow) = h;
+                *reinterpret_cast<__nv_bfloat162 *>(a.o_lo + n * a.opitch + grow) = l;
+            } else {
+                a.o_hi[n * a.opitch + grow] = h.x;
+                a.o_lo[n * a.opitch + grow] = l.x;
+            }
+        }
+        return;
+    }
+
+    const double g2 = 2.0 * a.gamma;
+    const float g2f = float(g2);
+    if (a.vec_f32 && (a.N % 4) == 0) {
+        const float *u = static_cast<const float *>(a.u);
+        float *q = static_cast<float *>(a.q);
+        const int rstage = a.restrict_stage;
+        if (rstage == 2) {
+            if (tid < FIN_RB) {
+                const int64_t grow = r0 + tid;
+                float qm = 0.f;
+                if (grow < a.M) {
+                    const int m = a.mrow[grow];
+                    float lx = 0.f;
+                    if (g2f != 0.f) {
+                        const float xc = u[grow * a.N + m];
+                        if (grow < a.M - 1) lx += xc - u[(grow + 1) * a.N + m];
+                        if (grow > 0) lx += xc - u[(grow - 1) * a.N + m];
+                    }
+                    qm = fmaf(g2f, lx, 2.f * zs[tid * LD + (m - int(n0))]);
+                }
+                qm_s[tid] = qm;
+            }
+            __syncthreads();
+        }
+        // a thread takes 4 consecutive columns (float4) of FIN_RB / RPI rows;
+        // all loads of a pass are issued before any is used
+        constexpr int CG = BN / 4;
+        constexpr int RPI = FIN_T / CG;
+        constexpr int PASSES = FIN_RB / RPI;
+        const int cc = (tid % CG) * 4;
+        const int64_t n = n0 + cc;
+        float pq_acc = 0.f;
+        float4 uc[PASSES], ud[PASSES], uu[PASSES], pv[PASSES];
+        uchar4 fm[PASSES];
+#pragma unroll
+        for (int j = 0; j < PASSES; ++j) {
+            const int64_t grow = r0 + j * RPI + tid / CG;
+            const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+            uc[j] = ud[j] = uu[j] = pv[j] = z4;
+            fm[j] = make_uchar4(0, 0, 0, 0);
+            if (grow < a.M && n < a.N) {
+                if (rstage != 0) {
+                    fm[j] = *reinterpret_cast<const uchar4 *>(a.freem + grow * a.N + n);
+                    pv[j] = *reinterpret_cast<const float4 *>(a.pvec + grow * a.N + n);
+                }
+                if (g2f != 0.f) {
+                    uc[j] = *reinterpret_cast<const float4 *>(u + grow * a.N + n);
+                    if (grow < a.M - 1) ud[j] = *reinterpret_cast<const float4 *>(u + (grow + 1) * a.N + n);
+                    if (grow > 0) uu[j] = *reinterpret_cast<const float4 *>(u + (grow - 1) * a.N + n);
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < PASSES; ++j) {
+            const int rr = j * RPI + tid / CG;
+            const int64_t grow = r0 + rr;
+            if (grow >= a.M || n >= a.N) continue;
+            const bool has_d = grow < a.M - 1, has_u = grow > 0;
+            const float *zr = &zs[rr * LD + cc];
+            float4 o;
+            o.x = fmaf(g2f, (has_d ? uc[j].x - ud[j].x : 0.f) + (has_u ? uc[j].x - uu[j].x : 0.f), 2.f * zr[0]);
+            o.y = fmaf(g2f, (has_d ? uc[j].y - ud[j].y : 0.f) + (has_u ? uc[j].y - uu[j].y : 0.f), 2.f * zr[1]);
+            o.z = fmaf(g2f, (has_d ? uc[j].z - ud[j].z : 0.f) + (has_u ? uc[j].z - uu[j].z : 0.f), 2.f * zr[2]);
+            o.w = fmaf(g2f, (has_d ? uc[j].w - ud[j].w : 0.f) + (has_u ? uc[j].w - uu[j].w : 0.f), 2.f * zr[3]);
+            if (rstage != 0) {
+                const float qm = rstage == 2 ? qm_s[rr] : 0.f;
+                o.x = fm[j].x ? o.x - qm : 0.f;
+                o.y = fm[j].y ? o.y - qm : 0.f;
+                o.z = fm[j].z ? o.z - qm : 0.f;
+                o.w = fm[j].w ? o.w - qm : 0.f;
+                pq_acc = fmaf(pv[j].x, o.x, pq_acc);
+                pq_acc = fmaf(pv[j].y, o.y, pq_acc);
+                pq_acc = fmaf(pv[j].z, o.z, pq_acc);
+                pq_acc = fmaf(pv[j].w, o.w, pq_acc);
+            }
+            *reinterpret_cast<float4 *>(q + grow * a.N + n) = o;
+        }
+        if (rstage != 0) {
+            double v[1] = {double(pq_acc)};
+            DevScalars *sc = a.sc;
+            grid_reduce<1>(v, a.red_part, a.red_stride, &sc->ticket[0], [sc](const double *t) {
+                sc->pq = t[0];
+                if (!(t[0] > 0.0)) sc->cg_active = 0;
+                else sc->alpha = sc->rz / t[0];
+            });
+        }
+        (void)lane;
+        return;
+    }
+    // double vectors (or N not a multiple of 4): q = 2 Z + 2 gamma L u
+    for (int e = tid; e < IE; e += FIN_T) {
+        const int rr = e / BN, cc = e % BN;
+        const int64_t grow = r0 + rr, n = n0 + cc;
+        if (grow >= a.M || n >= a.N) continue;
+        const int64_t k = grow * a.N + n;
+        const float z = zs[rr * LD + cc];
+        if (a.vec_f32) {
+            const float *u = static_cast<const float *>(a.u);
+            float lx = 0.f;
+            if (g2f != 0.f) {
+                const float xi = u[k];
+                if (grow < a.M - 1) lx += xi - u[k + a.N];
+                if (grow > 0) lx += xi - u[k - a.N];
+            }
+            static_cast<float *>(a.q)[k] = fmaf(g2f, lx, 2.f * z);
+        } else {
+            const double *u = static_cast<const double *>(a.u);
+            double lx = 0.0;
+            if (g2 != 0.0) {
+                const double xi = u[k];
+                if (grow < a.M - 1) lx += xi - u[k + a.N];
+                if (grow > 0) lx += xi - u[k - a.N];
+            }
+            static_cast<double *>(a.q)[k] = 2.0 * double(z) + g2 * lx;
+        }
+    }
 }
 
 // ----------------------------------------------------------------------------
@@ -808,6 +720,12 @@ static cudaError_t launch_tc_t(Plan &p, const TcArgs &a)
     dim3 grid(unsigned(S.n_ctas), unsigned((p.N + BN - 1) / BN));
     kern<<<grid, TC_THREADS, smem, p.stream>>>(a);
     count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // the split-K combination and the epilogue, a 32-row slice per CTA
+    dim3 fgrid(unsigned((FWD ? p.fwd_tiles : p.adj_tiles) * (TILE_R / FIN_RB)), unsigned((p.N + BN - 1) / BN));
+    k_tc_finish<BN, FWD><<<fgrid, FIN_T, 0, p.stream>>>(a);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -841,18 +759,17 @@ static TcArgs tc_args(Plan &p, bool fwd, const int32_t *gate)
     a.gamma = p.gamma;
     a.restrict_stage = 0;
     a.freem = p.freem; a.mrow = p.mrow; a.pvec = reinterpret_cast<const float *>(p.p);
-    a.pq_part = p.partials + 3 * p.max_partials;
-    a.pq_ticket = &p.sc->ticket[1];
+    a.red_part = p.partials;
+    a.red_stride = p.max_partials;
     a.sc = p.sc;
-    a.n_tiles = p.adj_tiles;
     a.wait_limit = TC_WAIT_LIMIT;
     a.skip_mma = 0;
     return a;
 }
 
-// HV = 2 F^T (F V) + 2 gamma L V on the tensor cores (three launches: the
-// transposed split copy of V, the forward tile product, the adjoint tile
-// product with the smoothness term).
+// HV = 2 F^T (F V) + 2 gamma L V on the tensor cores (five launches: the
+// transposed split copy of V, the forward tile product and its finish, the
+// adjoint tile product and its finish with the smoothness term).
 bool tc_restrict_fusable(const Plan &p)
 {
     return p.cg_f32 && band_bn(p.N) >= p.N && (p.N % 4) == 0;
