@@ -38,11 +38,12 @@ UNIT = "POVM-elem*iters/s"
 GAP = 1e-8
 CHOSEN = "tc"
 REF_ITERS = 4
-# DRAM bytes (read + write) of one tensor-core Hessian product, forward +
-# adjoint band contraction, from `ncu --set full` on the late-phase CG of the
-# c2 workload (profiles/k_band_tc_c2_hvp.md); the transpose kernel is not
-# included.  Must be reset to None whenever k_band_tc changes.
-TC_HVP_DRAM_BYTES = 5.136896e6 + 12.264704e6
+# DRAM bytes (read + write) of one tensor-core Hessian product (forward and
+# adjoint contraction and their finish kernels), from `ncu --set full` on the
+# late-phase CG of the c2 workload with ncu's cold caches
+# (profiles/k_band_tc_c2_hvp.md); the transpose kernel is not included.  Must
+# be reset to None whenever k_band_tc or k_tc_finish changes.
+TC_HVP_DRAM_BYTES = 5.120256e6 + 12.728576e6 + 7.488e6 + 16.370944e6
 WORKLOAD = "c2: M=4096 N=128 D=8192, 127-bin eta=0.8 dark=1e-4, lambda lin [0,3000], 1e7 shots, gamma=1e-2, band +-10sqrt(lambda)"
 
 
@@ -274,8 +275,8 @@ def main():
     achieved = flops / (hvp_ms * 1e-3) / 1e12
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": TC_HVP_DRAM_BYTES if CHOSEN == "tc" else None,
-                "traffic_unit": "bytes per Hessian product (ncu dram read+write, forward+adjoint)",
-                "kernel": "CG Hessian product: k_transpose_split + k_band_tc<fwd> + k_band_tc<adj>",
+                "traffic_unit": "bytes per Hessian product (ncu dram read+write, cold caches; contractions + finish kernels)",
+                "kernel": "CG Hessian product: k_transpose_split + k_band_tc<fwd> + k_tc_finish<fwd> + k_band_tc<adj> + k_tc_finish<adj>",
                 "avg_launch_ms": hvp_ms, "algorithmic_flops_per_launch": flops,
                 "peak_source": peak_src,
                 "note": "bf16 hi/lo split issues 3 MMAs per slice: tensor work is 3x the algorithmic flops"}
