@@ -224,6 +224,21 @@ typedef struct {
 
 tomo_status tomo_plan_info(tomo_plan_t plan, tomo_plan_info_t *info);
 
+/* The work-unit planning of the tensor-core contractions, host only (no
+ * device work), exposed so that schedules can be checked without a GPU:
+ * tile t reduces over [st[t], en[t]) (multiples of align; en <= st: empty);
+ * the ranges, laid end to end, are cut into at most `ctas` equal shares
+ * (multiples of align), a share crossing a tile boundary becoming one unit
+ * per tile, no unit longer than max_unit (a multiple of align), empty tiles
+ * one zero-length unit each, spread over the CTAs.  Writes up to `capacity`
+ * units as (tile, chunk, k0, k1) int32 quadruples in CTA order, the CTA
+ * boundaries (n_ctas + 1 entries, at most ctas + 1), the units per tile, and
+ * n_ctas; returns the number of units, or -1 (EINVAL in tomo_last_error) on
+ * invalid arguments or too small a capacity.  The paper has no counterpart. */
+int64_t tomo_plan_tc_units(const int64_t *st, const int64_t *en, int32_t tiles, int32_t align,
+                           int64_t max_unit, int64_t ctas, int32_t *units_out, int64_t capacity,
+                           int32_t *cta_first_out, int32_t *nsplit_out, int32_t *n_ctas_out);
+
 /* Self-test of the bounded device waits (no counterpart in the paper): runs
  * one tensor-core Hessian product whose tensor-core instructions are
  * withheld and whose mbarrier waits are bounded at 4096 polls, so every wait

@@ -90,6 +90,8 @@ EXPORTS = [
     ("tomo_hess_diag", c_i32, [c_ptr, c_ptr]),
     ("tomo_plan_info", c_i32, [c_ptr, ctypes.POINTER(tomo_plan_info_t)]),
     ("tomo_selftest_tc_timeout", c_i32, [c_ptr]),
+    ("tomo_plan_tc_units", c_i64, [c_ptr, c_ptr, c_i32, c_i32, c_i64, c_i64, c_ptr, c_i64, c_ptr, c_ptr,
+                                   ctypes.POINTER(c_i32)]),
     ("tomo_project_simplex", c_i32, [c_ptr, c_ptr, c_ptr]),
     ("tomo_smooth", c_i32, [c_ptr, c_ptr, c_ptr, c_i64, c_dbl]),
     ("tomo_infidelity", c_i32, [c_ptr, c_ptr, c_ptr, c_ptr]),
@@ -538,3 +540,23 @@ def fit_warm(plan, ws, P, **opts):
             return Th, rep, True
     Th, rep = plan.fit(P, **opts)
     return Th, rep, False
+
+
+def plan_tc_units(st, en, align=64, max_unit=1024, ctas=152):
+    """Host-only tensor-core work-unit planning (tomo_plan_tc_units): returns
+    (units as an (n, 4) int32 array of tile, chunk, k0, k1 in CTA order,
+    CTA boundaries, units per tile)."""
+    st = np.ascontiguousarray(st, dtype=np.int64)
+    en = np.ascontiguousarray(en, dtype=np.int64)
+    tiles = st.shape[0]
+    cap = int(np.sum(np.maximum(en - st, 0)) // align + 2 * tiles + 8)
+    units = np.empty((cap, 4), dtype=np.int32)
+    cta_first = np.empty(ctas + 1, dtype=np.int32)
+    nsplit = np.empty(tiles, dtype=np.int32)
+    nc = c_i32()
+    n = lib().tomo_plan_tc_units(st.ctypes.data, en.ctypes.data, tiles, align, max_unit, ctas,
+                                 units.ctypes.data, cap, cta_first.ctypes.data, nsplit.ctypes.data,
+                                 ctypes.byref(nc))
+    if n < 0:
+        raise TomoError(1, "tomo_plan_tc_units", tomo_last_error())
+    return units[:n].copy(), cta_first[:nc.value + 1].copy(), nsplit

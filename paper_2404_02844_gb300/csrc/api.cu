@@ -172,27 +172,21 @@ static tomo_status check_finite(Plan &p, const double *x, int64_t n, const char 
     return TOMO_OK;
 }
 
-// Tensor-core schedule, one wave of persistent CTAs: the reduction ranges of
-// all tiles, laid end to end, are cut into `ctas` shares of equal length
-// (multiples of `align`); a share that crosses a tile boundary becomes one
-// unit per tile it touches, and no unit is longer than max_unit (the size of
-// the per-unit tables in shared memory).  CTA c runs its units in order; the
-// units of one tile still combine through the split-K partials, so the
-// result does not depend on which CTA finishes a tile last.
-static cudaError_t make_schedule_tc(Plan &p, Schedule &S, const std::vector<int64_t> &st,
-                                    const std::vector<int64_t> &en, int align, int64_t max_unit,
-                                    int64_t ctas, int64_t *max_ctas)
+// Host planning of a tensor-core schedule, a pure function of the tiles'
+// reduction ranges [st, en): units in CTA order, the CTA boundaries and the
+// number of units per tile (see make_schedule_tc).
+static void plan_tc_units(const int64_t *st, const int64_t *en, int tiles, int align, int64_t max_unit,
+                          int64_t ctas, std::vector<WorkUnit> &units, std::vector<int32_t> &cta_first,
+                          std::vector<int32_t> &nsplit)
 {
-    const int tiles = int(st.size());
-    const int bn = band_bn(p.N);
-    const int64_t ncol = (p.N + bn - 1) / bn;
     int64_t W = 0;
     for (int t = 0; t < tiles; ++t) W += std::max<int64_t>(0, en[t] - st[t]);
     if (ctas < 1) ctas = 1;
     int64_t share = (W + ctas - 1) / ctas;
     share = std::max<int64_t>(align, ((share + align - 1) / align) * align);
     std::vector<std::vector<WorkUnit>> per_cta(1);
-    std::vector<int32_t> first(tiles, 0), nsplit(tiles, 0), empty;
+    std::vector<int32_t> empty;
+    nsplit.assign(tiles, 0);
     int64_t room = share;
     for (int t = 0; t < tiles; ++t) {
         const int64_t len = en[t] - st[t];
@@ -218,12 +212,31 @@ static cudaError_t make_schedule_tc(Plan &p, Schedule &S, const std::vector<int6
         per_cta[size_t((int64_t(j) * nc) / int64_t(empty.size()))].push_back(WorkUnit{empty[j], 0, 0, 0});
         nsplit[empty[j]] = 1;
     }
-    std::vector<WorkUnit> units;
-    std::vector<int32_t> cta_first(1, 0);
+    units.clear();
+    cta_first.assign(1, 0);
     for (const auto &v : per_cta) {
         units.insert(units.end(), v.begin(), v.end());
         cta_first.push_back(int32_t(units.size()));
     }
+}
+
+// Tensor-core schedule, one wave of persistent CTAs: the reduction ranges of
+// all tiles, laid end to end, are cut into `ctas` shares of equal length
+// (multiples of `align`); a share that crosses a tile boundary becomes one
+// unit per tile it touches, and no unit is longer than max_unit (the size of
+// the per-unit tables in shared memory).  CTA c runs its units in order; every
+// unit writes its partial tile and the finish kernel combines each tile's
+// partials in unit order, so the result does not depend on the CTA timing.
+static cudaError_t make_schedule_tc(Plan &p, Schedule &S, const std::vector<int64_t> &st,
+                                    const std::vector<int64_t> &en, int align, int64_t max_unit,
+                                    int64_t ctas, int64_t *max_ctas)
+{
+    const int tiles = int(st.size());
+    const int bn = band_bn(p.N);
+    const int64_t ncol = (p.N + bn - 1) / bn;
+    std::vector<WorkUnit> units;
+    std::vector<int32_t> cta_first, nsplit, first(tiles, 0);
+    plan_tc_units(st.data(), en.data(), tiles, align, max_unit, ctas, units, cta_first, nsplit);
     // every unit writes a partial tile (the finish kernel combines them)
     int64_t slots = 0;
     for (int t = 0; t < tiles; ++t) { first[t] = int32_t(slots); slots += nsplit[t]; }
@@ -1042,6 +1055,39 @@ tomo_status tomo_hvp(tomo_plan_t plan, const double *V, double *HV)
     }
     CUDA_TRY(cudaStreamSynchronize(p->stream));
     return TOMO_OK;
+}
+
+int64_t tomo_plan_tc_units(const int64_t *st, const int64_t *en, int32_t tiles, int32_t align,
+                           int64_t max_unit, int64_t ctas, int32_t *units_out, int64_t capacity,
+                           int32_t *cta_first_out, int32_t *nsplit_out, int32_t *n_ctas_out)
+{
+    if (!st || !en || tiles < 1 || align < 1 || max_unit < align || (max_unit % align) != 0 ||
+        !units_out || !cta_first_out || !nsplit_out || !n_ctas_out) {
+        tomo_set_error(TOMO_EINVAL, "invalid argument");
+        return -1;
+    }
+    for (int32_t t = 0; t < tiles; ++t)
+        if (en[t] > st[t] && ((st[t] % align) != 0 || (en[t] % align) != 0)) {
+            tomo_set_error(TOMO_EINVAL, "tile ranges must be multiples of align");
+            return -1;
+        }
+    std::vector<WorkUnit> units;
+    std::vector<int32_t> cta_first, nsplit;
+    plan_tc_units(st, en, tiles, align, max_unit, ctas, units, cta_first, nsplit);
+    if (int64_t(units.size()) > capacity || int64_t(cta_first.size()) > ctas + 1) {
+        tomo_set_error(TOMO_EINVAL, "output capacity too small");
+        return -1;
+    }
+    for (size_t k = 0; k < units.size(); ++k) {
+        units_out[4 * k] = units[k].tile;
+        units_out[4 * k + 1] = units[k].chunk;
+        units_out[4 * k + 2] = units[k].k0;
+        units_out[4 * k + 3] = units[k].k1;
+    }
+    for (size_t k = 0; k < cta_first.size(); ++k) cta_first_out[k] = cta_first[k];
+    for (int32_t t = 0; t < tiles; ++t) nsplit_out[t] = nsplit[size_t(t)];
+    *n_ctas_out = int32_t(cta_first.size()) - 1;
+    return int64_t(units.size());
 }
 
 tomo_status tomo_plan_info(tomo_plan_t plan, tomo_plan_info_t *info)
