@@ -10,8 +10,8 @@
 // Operands are bf16 in shared memory, K-major, 128-byte swizzled; the
 // accumulator is f32 in tensor memory.  Precision is recovered by splitting
 // every operand into hi + lo bf16 parts and accumulating hi*hi + hi*lo +
-// lo*hi (three MMAs per K slice, ~17 significant bits; the lo*lo term is
-// below f32 rounding of the accumulator's scale).  The weights F are generated
+// lo*hi (three MMAs per K slice, ~17 significant bits: the dropped lo*lo
+// term is of the order of what the two-part split itself leaves, 2^-18).  The weights F are generated
 // by all 256 threads straight into the swizzled A tile (runs of 8 photon
 // numbers from the log-space anchors, exact ratio recurrence in float); the
 // vector operand comes from a transposed bf16 hi/lo copy (rows = outcomes,
