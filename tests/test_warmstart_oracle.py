@@ -1,11 +1,14 @@
 """Pins of the learned-warm-start oracle (oracle/warmstart.py): its gradient
-against central differences, its convolution against numpy's correlate, the
-softmax's simplex rows, the first Adam step's closed form and the bf16
-rounding against torch's conversion."""
+against central differences (and planted mistakes that this pin catches), its
+convolution against numpy's correlate, the softmax's simplex rows, the first
+Adam step's closed form, the bf16 rounding against torch's conversion, and
+the warm-start population's outcome probabilities against the shared
+generator's windowed sum."""
 import numpy as np
 import pytest
 
 from oracle import warmstart as ws
+import workloads
 
 TINY = ws.Shape(D=16, C0=4, M=6, C1=3, C2=2, K=3, S1=2, S2=2, H=3)
 
@@ -85,3 +88,53 @@ def test_bf16_rounding_matches_torch():
     # ties go to the even neighbour
     assert ws.round_bf16(np.array([1 + 2.0 ** -8]))[0] == 1.0
     assert ws.round_bf16(np.array([1 + 3 * 2.0 ** -8]))[0] == 1 + 2.0 ** -6
+
+
+# Plausible mistakes planted in copies of the oracle's functions: each must
+# make the central-difference pin fail (the pin catches them).
+def _fd_mismatch(loss_and_grad):
+    rng = np.random.default_rng(3)
+    theta = rng.standard_normal(TINY.count()) * 0.5
+    Ps, Ts, ncols = tiny_batch(rng)
+    _, g = loss_and_grad(TINY, theta, Ps, Ts, ncols)
+    h = 1e-6
+    worst = 0.0
+    for j in rng.choice(TINY.count(), 80, replace=False):
+        tp, tm = theta.copy(), theta.copy()
+        tp[j] += h
+        tm[j] -= h
+        fd = (ws.loss_and_grad(TINY, tp, Ps, Ts, ncols)[0] - ws.loss_and_grad(TINY, tm, Ps, Ts, ncols)[0]) / (2 * h)
+        worst = max(worst, abs(fd - g[j]) / max(1.0, abs(fd)))
+    return worst
+
+
+@pytest.mark.parametrize("mutant", ["leaky_forward_relu_backward", "softmax_columns_permuted",
+                                    "conv_backward_stride_ignored"])
+def test_gradient_pin_catches_planted_mistakes(monkeypatch, mutant):
+    assert _fd_mismatch(ws.loss_and_grad) <= 1e-6
+    if mutant == "leaky_forward_relu_backward":
+        # the backward pass uses (Y > 0) masks; a leaky forward disagrees
+        monkeypatch.setattr(ws, "relu", lambda x: np.where(x > 0, x, 0.1 * x))
+    elif mutant == "softmax_columns_permuted":
+        orig = ws.masked_softmax
+
+        def bad(Z, ncols):
+            out = orig(Z, ncols)
+            return out[:, ::-1].copy() if ncols == Z.shape[1] else out
+        monkeypatch.setattr(ws, "masked_softmax", bad)
+    else:
+        orig = ws.conv1d_backward
+        monkeypatch.setattr(ws, "conv1d_backward", lambda X, W, dY, S: orig(X, W, dY, 1))
+    assert _fd_mismatch(ws.loss_and_grad) > 1e-4
+
+
+def test_c5_population_outcomes_match_the_windowed_generator():
+    """The warm-start population's dense F q equals the windowed scipy sum
+    of the shared generator (two independent evaluations)."""
+    M, D, X = 300, 400, 200.0
+    lam = workloads.probe_intensities(D, X)
+    F = workloads.dense_poisson(M, lam)
+    w = workloads.config_c5_instance(3, F=F, M=M, D=D, X=X, shots=None, bins_range=(4, 15))
+    q = workloads.outcome_probabilities(lam, w.theta_true)
+    np.testing.assert_allclose(w.P, q, rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(w.theta_true.sum(1), 1.0, atol=1e-13)
