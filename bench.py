@@ -262,8 +262,8 @@ def main():
     ttt = T / args.steps
 
     # dominant kernel: the CG Hessian product (forward + adjoint band
-    # contraction on the tensor cores), timed live with CUDA events on the
-    # plan stream inside the timed solves
+    # contraction on the tensor cores and their finish kernels), timed live
+    # with CUDA events on the plan stream inside the last timed solve
     hvp_ms = sum(r["fwd_ms"] + r["adj_ms"] for r in reps) / max(1, sum(r["fwd_count"] for r in reps))
     flops = 4.0 * nnz * N           # 2 F^T (F v): two band contractions of 2 nnz N flop
     peaks = measured_peaks()
