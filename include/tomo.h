@@ -148,7 +148,27 @@ typedef struct {
     int32_t profile;       /* 0; 1: time every band contraction of the CG loop
                               with CUDA events on the plan stream (report fields
                               fwd_ms / adj_ms); adds no synchronisation */
+    int32_t trace_len;     /* 0; > 0: rows of `trace` (one per Newton iteration) */
+    /* CG forcing term (App. B leaves the CG stop open): CG stops when
+     * ||r|| <= eta ||b||, eta = min(cg_eta_max, ||b||^cg_eta_pow), b the
+     * right-hand side (minus the free gradient); cg_eta_pow = 0 gives the
+     * constant eta = cg_eta_max. */
+    double cg_eta_max;     /* 0.5 */
+    double cg_eta_pow;     /* 0.5 */
+    double max_seconds;    /* 0: off; > 0: stop (stop code 2) once the solve has
+                              run this long on the host clock */
+    double *trace;         /* NULL, or a HOST array of trace_len x TOMO_TRACE_COLS
+                              doubles: per Newton iteration k, row k receives
+                              (stage, f before the step, KKT residual before the
+                              step, CG products, ||r|| / ||b|| reached by the CG
+                              recursion, accepted step length (0: none),
+                              line-search trials, host ms since the start,
+                              trials rejected for a negative implicit entry
+                              (stage 2), how CG ended: 0 forcing test,
+                              1 product cap, 2 non-positive curvature) */
 } tomo_fit_opts;
+
+#define TOMO_TRACE_COLS 10
 
 /* Result of a fit. */
 typedef struct {
@@ -359,7 +379,9 @@ int64_t tomo_kernel_launches(void);
  * *f (one double, DEVICE memory) receives f = ||P - F Theta||^2 + gamma
  * sum_n sum_{i<M-1} (Theta_{i,n} - Theta_{i+1,n})^2 in double, with the band
  * of band_k as in tomo_desc.  lambda (D), P (D x N) and Theta (M x N) are
- * DEVICE pointers; lambda need not be sorted.  Work is queued on `stream`
+ * DEVICE pointers; lambda need not be sorted, and every entry must be
+ * finite and >= 0 (it is in device memory, so the call cannot check it on
+ * the host: an invalid entry makes *f NaN).  Work is queued on `stream`
  * (cudaStream_t, NULL: the legacy default stream); the call returns without
  * waiting, f is ready when the stream reaches it.
  *

@@ -49,7 +49,8 @@ class _Opts(ctypes.Structure):
     _fields_ = [("eps_kkt", c_dbl), ("eps_bar", c_dbl), ("beta", c_dbl), ("c", c_dbl),
                 ("switch_tol", c_dbl), ("f_target", c_dbl), ("max_newton", c_i64),
                 ("max_stage1", c_i64), ("max_cg", c_i64), ("ls_max", c_i64),
-                ("start_stage", c_i64), ("warm_start", c_i64), ("stall_iters", c_i64)]
+                ("start_stage", c_i64), ("warm_start", c_i64), ("stall_iters", c_i64),
+                ("cg_eta_max", c_dbl), ("cg_eta_pow", c_dbl)]
 
 
 class _Report(ctypes.Structure):

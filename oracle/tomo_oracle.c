@@ -32,8 +32,9 @@
  *           k <= 0 keeps the full range (dense F).
  *   I set:  eps_k = min(eps_bar, w_k), w_k = || x - P(x - grad) ||_2 with P the
  *           stage's projection (simplex rows in stage 1, max(0,.) in stage 2).
- *   CG:     p0 = 0; stop when ||r|| <= min(0.5, sqrt(||b||)) ||b|| or after
- *           max_cg (default 500) Hessian products; non-descent result ->
+ *   CG:     p0 = 0; stop when ||r|| <= eta ||b||, eta = min(eta_max,
+ *           ||b||^eta_pow) (default min(0.5, sqrt(||b||))), or after max_cg
+ *           (default 500) Hessian products; non-descent result ->
  *           p = -grad / diag.
  *   Armijo: accept the smallest m with f(x(beta^m)) <= f(x) + c grad^T
  *           (x(beta^m) - x) (projected-arc form), beta = 3/4, c = 1/10.
@@ -520,6 +521,8 @@ typedef struct {
     int64_t start_stage; /* 1: Algorithm 3; 2: stage 2 only (Algorithm 1) */
     int64_t warm_start;  /* 0: Theta^(0) = 1/N, 1: use Theta as given */
     int64_t stall_iters; /* stop after this many iterations without decrease */
+    double cg_eta_max;   /* CG forcing term eta = min(cg_eta_max, ||b||^cg_eta_pow) */
+    double cg_eta_pow;
 } orc_opts;
 
 typedef struct {
@@ -545,6 +548,8 @@ ORC_API void orc_default_opts(orc_opts *o)
     o->start_stage = 1;
     o->warm_start = 0;
     o->stall_iters = 5;
+    o->cg_eta_max = 0.5;
+    o->cg_eta_pow = 0.5;
 }
 
 typedef struct {
@@ -605,7 +610,14 @@ static int64_t newton_direction(const orc_problem *p, int stage, orc_work *w,
         w->pv[k] = w->z[k];
     }
     double bn = sqrt(dot(w->r, w->r, MN));
-    double eta = sqrt(bn) < 0.5 ? sqrt(bn) : 0.5;
+    /* forcing term: min(eta_max, ||b||^eta_pow); the default 0.5, 0.5 is the
+     * truncated-Newton choice min(0.5, sqrt||b||) */
+    double pw;
+    if (o->cg_eta_pow == 0.5) pw = sqrt(bn);
+    else if (o->cg_eta_pow == 1.0) pw = bn;
+    else if (o->cg_eta_pow == 0.0) pw = 1.0;
+    else pw = pow(bn, o->cg_eta_pow);
+    double eta = pw < o->cg_eta_max ? pw : o->cg_eta_max;
     double tol = eta * bn;
     double rz = dot(w->r, w->z, MN);
     int64_t it = 0;

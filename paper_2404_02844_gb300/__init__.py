@@ -47,7 +47,12 @@ class tomo_fit_opts(ctypes.Structure):
                 ("switch_tol", c_dbl), ("f_target", c_dbl), ("max_newton", c_i32),
                 ("max_stage1", c_i32), ("max_cg", c_i32), ("ls_max", c_i32),
                 ("start_stage", c_i32), ("warm_start", c_i32), ("stall_iters", c_i32),
-                ("refresh_every", c_i32), ("profile", c_i32)]
+                ("refresh_every", c_i32), ("profile", c_i32), ("trace_len", c_i32),
+                ("cg_eta_max", c_dbl), ("cg_eta_pow", c_dbl), ("max_seconds", c_dbl),
+                ("trace", c_ptr)]
+
+TRACE_COLS = 10
+TRACE_NAMES = ("stage", "f", "kkt", "cg", "cg_rel_res", "alpha", "ls", "ms", "ls_neg", "cg_end")
 
 
 class tomo_fit_report(ctypes.Structure):
@@ -357,10 +362,15 @@ class Plan:
         """Algorithm 3.  Returns (Theta, report dict).  Theta (if given) is
         the warm start and is overwritten with the result."""
         o = tomo_fit_opts_default()
+        trace = opts.pop("trace", 0)
         for k, v in opts.items():
-            if not hasattr(o, k):
+            if not hasattr(o, k) or k in ("trace", "trace_len"):
                 raise KeyError(k)
             setattr(o, k, v)
+        tr = None
+        if trace:
+            tr = np.zeros((int(trace), TRACE_COLS))
+            o.trace, o.trace_len = tr.ctypes.data, int(trace)
         if Theta is None:
             Theta = np.empty((self.M, self.N)) if isinstance(P, np.ndarray) \
                 else self._dev_empty(self.M, self.N)
@@ -369,6 +379,8 @@ class Plan:
         st, rep = tomo_fit(self._h, _ptr(P), _ptr(Theta), o)
         d = _fit_dict(rep)
         d["status"] = STATUS[st]
+        if tr is not None:
+            d["trace"] = tr[:rep.iters_s1 + rep.iters_s2]
         return Theta, d
 
     def apply_F(self, X):

@@ -144,7 +144,8 @@ static tomo_status stage_in(Plan &p, const double *src, int64_t count, double **
 }
 
 // A bounded mbarrier wait of a tensor-core contraction gave up (the kernel
-// set tc_err and stopped its remaining work): report it once and re-arm.
+// set tc_err and skipped its remaining units; the finish kernels, which need
+// no counters, still ran to their end): report it once and clear the flag.
 static tomo_status check_tc_err(Plan &p)
 {
     if (!hvp_on_tensor_cores(p.precision)) return TOMO_OK;
@@ -152,13 +153,7 @@ static tomo_status check_tc_err(Plan &p)
     CUDA_TRY(cudaMemcpyAsync(&err, &p.sc->tc_err, sizeof(err), cudaMemcpyDeviceToHost, p.stream));
     CUDA_TRY(cudaStreamSynchronize(p.stream));
     if (!err) return TOMO_OK;
-    // a CTA that gave up skipped its remaining units: the split-K counters
-    // and the fused-restriction ticket may be left mid-count, so re-arm them
     CUDA_TRY(cudaMemsetAsync(&p.sc->tc_err, 0, sizeof(int32_t), p.stream));
-    CUDA_TRY(cudaMemsetAsync(&p.sc->ticket[1], 0, sizeof(unsigned int), p.stream));
-    const int64_t ncol = (p.N + band_bn(p.N) - 1) / band_bn(p.N);
-    CUDA_TRY(cudaMemsetAsync(p.sched_tc[0].counters, 0, sizeof(unsigned) * size_t(p.fwd_tiles * ncol), p.stream));
-    CUDA_TRY(cudaMemsetAsync(p.sched_tc[1].counters, 0, sizeof(unsigned) * size_t(p.adj_tiles * ncol), p.stream));
     CUDA_TRY(cudaStreamSynchronize(p.stream));
     return fail(TOMO_ETIMEOUT, "a bounded tensor-core pipeline wait gave up");
 }
@@ -553,6 +548,11 @@ void tomo_fit_opts_default(tomo_fit_opts *o)
     o->stall_iters = 5;
     o->refresh_every = 8;
     o->profile = 0;
+    o->trace_len = 0;
+    o->cg_eta_max = 0.5;
+    o->cg_eta_pow = 0.5;
+    o->max_seconds = 0.0;
+    o->trace = nullptr;
 }
 
 tomo_status tomo_plan(tomo_plan_t *out, const tomo_desc *d)
@@ -784,6 +784,7 @@ static tomo_status run_cg_chunk(Plan &p, int stage, const ChunkEvents *evs)
 struct LsResult {
     bool ok;
     double f_new, gts, alpha;
+    int neg;      // trials rejected because an implicit entry went negative
 };
 
 // Backtracking line search of App. B along dir (or -g/diag when the device
@@ -795,6 +796,7 @@ static tomo_status line_search(Plan &p, int stage, const double *P, double f,
                                const tomo_fit_opts &o, bool delta, int32_t *ls_count, LsResult *res)
 {
     res->ok = false;
+    res->neg = 0;
     double alpha = 1.0;
     for (int m = 0; m < o.ls_max; ++m, alpha *= o.beta) {
         ++*ls_count;
@@ -805,7 +807,10 @@ static tomo_status line_search(Plan &p, int stage, const double *P, double f,
             CUDA_TRY(launch_forward_gated_ls(p, TOMO_PREC_FP64, FWD_RESID, p.trial, p.Rt, P));
         TOMO_TRY(read_scalars(p));
         const DevScalars &s = *p.sc_host;
-        if (s.neg) continue;
+        if (s.neg) {
+            ++res->neg;
+            continue;
+        }
         bool accept;
         double fn;
         if (delta) {
@@ -841,12 +846,18 @@ static tomo_status fit_impl(Plan &p, const double *P, const tomo_fit_opts &o, to
     int stage = o.start_stage == 2 ? 2 : 1;
     int stall = 0, since_refresh = 0;
     rep.stop = 2;
+    const auto t_start = std::chrono::steady_clock::now();
+    auto elapsed_ms = [&]() {
+        return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+    };
     for (int k = 0; k < o.max_newton; ++k) {
+        if (o.max_seconds > 0.0 && elapsed_ms() >= 1e3 * o.max_seconds) break;
+        double *trow = k < o.trace_len ? o.trace + size_t(k) * TOMO_TRACE_COLS : nullptr;
         // gradient G = 2 F^T R + 2 gamma L Theta
         CUDA_TRY(launch_adjoint(p, prec_gradient(p.precision), ADJ_GRAD, p.R, p.G, p.Th, false));
         if (stage == 1 && rep.iters_s1 >= o.max_stage1) stage = 2;
         CUDA_TRY(launch_setup1(p, stage, o.eps_bar));
-        CUDA_TRY(launch_setup2(p, stage, o.max_cg));
+        CUDA_TRY(launch_setup2(p, stage, o.max_cg, o.cg_eta_max, o.cg_eta_pow));
         TOMO_TRY(read_scalars(p));
         const double kkt = std::sqrt(p.sc_host->kkt2 / MN);
         if (!std::isfinite(kkt) || !std::isfinite(f))
@@ -866,6 +877,10 @@ static tomo_status fit_impl(Plan &p, const double *P, const tomo_fit_opts &o, to
         while (active) {
             TOMO_TRY(run_cg_chunk(p, stage, o.profile ? &evs : nullptr));
             TOMO_TRY(read_scalars(p));
+            // a tensor-core wait that gave up leaves the product incomplete:
+            // stop at once (tomo_fit reports it and clears the flag)
+            if (p.sc_host->tc_err)
+                return fail(TOMO_ETIMEOUT, "a bounded tensor-core pipeline wait gave up (Newton iteration %d)", k);
             active = p.sc_host->cg_active;
             if (o.profile) {
                 // only the iterations that ran (the rest of the chunk exited
@@ -884,6 +899,17 @@ static tomo_status fit_impl(Plan &p, const double *P, const tomo_fit_opts &o, to
             done = p.sc_host->cg_iters;
         }
         rep.cg_total += p.sc_host->cg_iters;
+        if (trow) {
+            const DevScalars &c = *p.sc_host;
+            trow[0] = stage;
+            trow[1] = f;
+            trow[2] = kkt;
+            trow[3] = c.cg_iters;
+            trow[4] = c.bn > 0.0 ? std::sqrt(c.rr) / c.bn : 0.0;
+            trow[5] = 0.0;
+            trow[6] = rep.ls_total;
+            trow[9] = !(c.pq > 0.0) && c.cg_iters > 0 ? 2.0 : (c.cg_iters >= c.max_cg && !(std::sqrt(c.rr) <= c.tol)) ? 1.0 : 0.0;
+        }
         CUDA_TRY(launch_direction(p, stage));
         if (stage == 1) ++rep.iters_s1; else ++rep.iters_s2;
 
@@ -892,6 +918,12 @@ static tomo_status fit_impl(Plan &p, const double *P, const tomo_fit_opts &o, to
         if (!ls.ok) {
             CUDA_TRY(launch_set_grad_dir(p));
             TOMO_TRY(line_search(p, stage, P, f, o, delta, &rep.ls_total, &ls));
+        }
+        if (trow) {
+            trow[5] = ls.ok ? ls.alpha : 0.0;
+            trow[6] = rep.ls_total - trow[6];
+            trow[7] = elapsed_ms();
+            trow[8] = ls.neg;
         }
         if (!ls.ok) {
             if (stage == 1) { stage = 2; continue; }
@@ -940,7 +972,9 @@ tomo_status tomo_fit(tomo_plan_t plan, const double *P, double *Theta, const tom
     if (opts) o = *opts; else tomo_fit_opts_default(&o);
     if (!(o.beta > 0.0 && o.beta < 1.0) || !(o.c > 0.0 && o.c < 1.0) || o.max_newton < 0 ||
         o.max_cg < 0 || o.ls_max < 1 || !(o.eps_bar >= 0.0) || !(o.eps_kkt >= 0.0) ||
-        o.refresh_every < 1 || o.stall_iters < 1)
+        o.refresh_every < 1 || o.stall_iters < 1 || !(o.cg_eta_max > 0.0 && o.cg_eta_max < 1.0) ||
+        !(o.cg_eta_pow >= 0.0 && o.cg_eta_pow <= 2.0) || !(o.max_seconds >= 0.0) || o.trace_len < 0 ||
+        (o.trace_len > 0 && !o.trace))
         return fail(TOMO_EINVAL, "invalid options");
     tomo_fit_report rep;
     std::memset(&rep, 0, sizeof(rep));
@@ -973,8 +1007,13 @@ tomo_status tomo_fit(tomo_plan_t plan, const double *P, double *Theta, const tom
         CUDA_TRY(launch_fill(p, p.Th, 1.0 / double(p.N), MN));
     }
     tomo_status st = fit_impl(p, Pd, o, rep);
+    // the tensor-core flag is read and cleared on every exit path, so that a
+    // timeout is never reported by a later call; it is the root cause of any
+    // other failure of the same solve
+    const tomo_status te = check_tc_err(p);
+    if (te == TOMO_ETIMEOUT) return te;
     if (st != TOMO_OK) return st;
-    TOMO_TRY(check_tc_err(p));
+    TOMO_TRY(te);
     CUDA_TRY(cudaMemcpyAsync(Theta, p.Th, sizeof(double) * size_t(MN),
                              tdev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, p.stream));
     CUDA_TRY(cudaStreamSynchronize(p.stream));

@@ -59,6 +59,14 @@ k_objective_rows(int64_t M, int64_t N, int64_t D, const double *lam, double band
     constexpr int NPT = MAX_N / NOALLOC_THREADS;  // outcomes per thread
     for (int64_t d = blockIdx.x; d < D; d += gridDim.x) {
         const double x = lam[d];
+        if (!(x >= 0.0) || isinf(x)) {
+            // an invalid mean photon number (negative, NaN or infinite; the
+            // array lives in device memory, so the host cannot check it)
+            // makes the objective NaN instead of indexing with a band
+            // computed from it
+            if (tid == 0) scratch[d] = __longlong_as_double(0x7ff8000000000000LL);
+            continue;
+        }
         int64_t lo, hi;
         if (band_k <= 0.0) {
             lo = 0;
@@ -180,7 +188,7 @@ extern "C" tomo_status tomo_objective_noalloc(int64_t M, int64_t N, int64_t D, c
     if (!lambda || !P || !Theta || !f) return tomo_set_error(TOMO_EINVAL, "NULL argument");
     if (M < 1 || N < 2 || N > MAX_N || D < 1)
         return tomo_set_error(TOMO_EINVAL, "sizes out of range (M >= 1, 2 <= N <= 1024, D >= 1)");
-    if (D + M > TOMO_NOALLOC_MAX_ROWS)
+    if (D > TOMO_NOALLOC_MAX_ROWS || M > TOMO_NOALLOC_MAX_ROWS - D)
         return tomo_set_error(TOMO_EINVAL,
                               "D + M exceeds the scratch of tomo_objective_noalloc (TOMO_NOALLOC_MAX_ROWS = 262144)");
     if (!std::isfinite(gamma) || gamma < 0.0 || !std::isfinite(band_k))

@@ -242,7 +242,8 @@ __global__ void k_setup1(RowArgs a, int stage, double eps_bar, const double *Th,
 // u = E p (column m(i) := -sum of the others).
 // ---------------------------------------------------------------------------
 template <int VPL, typename VT>
-__global__ void k_setup2(RowArgs a, int stage, int max_cg, const double *Th, const double *g,
+__global__ void k_setup2(RowArgs a, int stage, int max_cg, double eta_max, double eta_pow,
+                         const double *Th, const double *g,
                          const uint8_t *var, const int32_t *mrow, uint8_t *freem, VT *x,
                          VT *r, VT *z, VT *p, VT *u)
 {
@@ -307,13 +308,14 @@ __global__ void k_setup2(RowArgs a, int stage, int max_cg, const double *Th, con
     ROW_LOOP_END
     double v[2] = {rz, rr};
     DevScalars *sc = a.sc;
-    grid_reduce<2>(v, a.partials, a.pstride, &sc->ticket[0], [sc, max_cg](const double *t) {
+    grid_reduce<2>(v, a.partials, a.pstride, &sc->ticket[0], [sc, max_cg, eta_max, eta_pow](const double *t) {
         sc->rz = t[0];
         sc->rr = t[1];
         const double bn = sqrt(t[1]);
-        const double sq = sqrt(bn);
+        // forcing term eta = min(eta_max, ||b||^eta_pow) (reading R5: 0.5, 0.5)
+        const double pw = eta_pow == 0.5 ? sqrt(bn) : eta_pow == 1.0 ? bn : eta_pow == 0.0 ? 1.0 : pow(bn, eta_pow);
         sc->bn = bn;
-        sc->tol = (sq < 0.5 ? sq : 0.5) * bn;
+        sc->tol = (pw < eta_max ? pw : eta_max) * bn;
         sc->cg_iters = 0;
         sc->max_cg = max_cg;
         sc->use_grad_dir = 0;
@@ -765,14 +767,14 @@ cudaError_t launch_setup1(Plan &p, int stage, double eps_bar)
     return cudaGetLastError();
 }
 
-cudaError_t launch_setup2(Plan &p, int stage, int max_cg)
+cudaError_t launch_setup2(Plan &p, int stage, int max_cg, double eta_max, double eta_pow)
 {
     RowArgs a = row_args(p);
     if (p.cg_f32)
-        VPL_DISPATCH_T(p.N, k_setup2, float, row_grid(p), a, stage, max_cg, p.Th, p.g, p.var, p.mrow,
+        VPL_DISPATCH_T(p.N, k_setup2, float, row_grid(p), a, stage, max_cg, eta_max, eta_pow, p.Th, p.g, p.var, p.mrow,
                        p.freem, CGV(p.x), CGV(p.r), CGV(p.z), CGV(p.p), CGV(p.u));
     else
-        VPL_DISPATCH_T(p.N, k_setup2, double, row_grid(p), a, stage, max_cg, p.Th, p.g, p.var, p.mrow,
+        VPL_DISPATCH_T(p.N, k_setup2, double, row_grid(p), a, stage, max_cg, eta_max, eta_pow, p.Th, p.g, p.var, p.mrow,
                        p.freem, p.x, p.r, p.z, p.p, p.u);
     return cudaGetLastError();
 }

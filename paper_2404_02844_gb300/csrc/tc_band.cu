@@ -19,8 +19,8 @@
 // swizzle chunk.  A single thread issues the MMAs of a stage and commits them
 // to the stage's mbarrier while the other threads already produce the next
 // stage (two stages).  The reduction range of every tile is cut into work
-// units (split-K, planned on the host); units of one tile write f32 partial
-// tiles and the last one to finish sums them in unit order.
+// units (split-K, planned on the host); every unit writes its f32 partial
+// tile and a finish kernel sums each tile's partials in unit order.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -253,8 +253,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(TcArgs a)
     const int64_t n0 = int64_t(blockIdx.y) * BN;
     bool ok = true;
     // pipeline steps issued by this CTA so far (stage and mbarrier phase of
-    // every step follow from it across units)
+    // every step follow from it across units), and the last step whose MMAs
+    // were committed (-1: none), known to every thread
     uint32_t gstep = 0;
+    int64_t committed = -1;
 
     // the CTA's units, in order (one wave of persistent CTAs)
     const int u_end = a.cta_first[blockIdx.x + 1];
@@ -397,7 +399,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(TcArgs a)
         else cp_async_wait_all();
         tc::fence_proxy_async_smem();
         tc::tc_fence_before_sync();
-        __syncthreads();
+        // a wait that gave up in any thread stops the CTA here, uniformly and
+        // before any further MMA is issued (the stages it would overwrite may
+        // still be read by MMAs in flight)
+        if (__syncthreads_or(ok ? 0 : 1)) {
+            ok = false;
+            break;
+        }
+        if (!a.skip_mma) committed = int64_t(g);
         if (tid == 0 && !a.skip_mma) {
             tc::tc_fence_after_sync();
             const uint32_t a_hi = tc::smem_u32(A_hi), a_lo = tc::smem_u32(A_lo);
@@ -415,13 +424,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(TcArgs a)
             tc::mma_commit(&bars[st]);
         }
     }
-    if (nsteps > 0) {
+    if (ok && nsteps > 0) {
         const uint32_t g = gstep + uint32_t(nsteps - 1);
         if (!tc::mbar_wait_bounded(&bars[g % TC_STAGES], (g / TC_STAGES) & 1u, a.wait_limit))
             ok = false;
     }
     gstep += uint32_t(nsteps);
     tc::tc_fence_after_sync();
+    if (__syncthreads_or(ok ? 0 : 1)) {
+        ok = false;
+        break;
+    }
 
     // ---- this unit's f32 partial tile (split-K) ----
     // through a shared-memory copy (the stage buffers: every MMA and copy of
@@ -459,14 +472,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(TcArgs a)
         for (int e = tid; e < TE; e += TC_THREADS) mine[e] = tile_s[(e / BN) * LD + (e % BN)];
     }
     // the next unit's first MMA overwrites the accumulator and its tables
-    // replace these: every thread is past its tensor-memory loads.  A wait
-    // that gave up in any thread ends the CTA's work (uniformly).
+    // replace these: every thread is past its tensor-memory loads
     tc::tc_fence_before_sync();
-    if (__syncthreads_or(ok ? 0 : 1)) {
-        ok = false;
-        break;
-    }
+    __syncthreads();
     }  // units
+    if (!ok) {
+        // the CTA gave up: no copy may still target its shared memory and no
+        // committed MMA may still write its tensor memory when it is freed,
+        // so wait for the copies and, once more with a bound, for the last
+        // committed group of MMAs (their completion covers all earlier ones)
+        cp_async_wait_all();
+        if (committed >= 0) {
+            const uint32_t g = uint32_t(committed);
+            tc::mbar_wait_bounded(&bars[g % TC_STAGES], (g / TC_STAGES) & 1u, a.wait_limit);
+        }
+        tc::tc_fence_after_sync();
+        __syncthreads();
+    }
     if (warp == 0) tc::tmem_dealloc(tmem, L::TMEM_COLS);
     if (!ok && tid == 0) atomicExch(a.err, 1);
 }

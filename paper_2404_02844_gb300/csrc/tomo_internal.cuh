@@ -158,7 +158,7 @@ cudaError_t launch_regulariser(Plan &p, const double *X);   // -> sc->regval
 cudaError_t launch_project_rows(Plan &p, const double *X, double *Y);
 cudaError_t launch_kkt(Plan &p, const double *Th, const double *G);  // -> sc->kkt2
 cudaError_t launch_setup1(Plan &p, int stage, double eps_bar);  // kkt2, w2, eps, g, var, mrow
-cudaError_t launch_setup2(Plan &p, int stage, int max_cg);      // I mask, CG start
+cudaError_t launch_setup2(Plan &p, int stage, int max_cg, double eta_max, double eta_pow);  // I mask, CG start
 cudaError_t launch_cg_restrict(Plan &p, int stage);
 cudaError_t launch_cg_update_xr(Plan &p, int stage);
 cudaError_t launch_cg_update_p(Plan &p, int stage);

@@ -2,8 +2,8 @@
 fixed number of Newton iterations (a representative mix of every kernel of
 the hot path), for use under ncu:
 
-    python -m paper_2404_02844_gb300.profile_target --config c2 --precision fp32 --newton 3
-    python -m paper_2404_02844_gb300.profile_target --config c2 --precision tc --newton 2 \
+    python profile_target.py --config c2 --precision fp32 --newton 3
+    python profile_target.py --config c2 --precision tc --newton 2 \
         --warm-newton 60      # late-phase CG iterations inside the NVTX range "profiled"
 """
 from __future__ import annotations
@@ -13,7 +13,7 @@ import os
 import sys
 import time
 
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 

@@ -84,3 +84,26 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(tomo):
     st = L.tomo_objective_noalloc(4, 3, 8, lam.data_ptr(), 10.0, 0.0, P.data_ptr(), Th.data_ptr(),
                                   None, stream)
     assert st == 1
+    # sizes whose sum overflows int64 are rejected too, before anything is read
+    big = 2 ** 62
+    st = L.tomo_objective_noalloc(big, 3, big, lam.data_ptr(), 10.0, 0.0, P.data_ptr(),
+                                  Th.data_ptr(), f_d.data_ptr(), stream)
+    assert st == 1
+
+
+def test_noalloc_invalid_lambda_gives_nan(tomo):
+    # lambda lives in device memory, so an invalid entry cannot be refused on
+    # the host: the objective comes back NaN instead of a value computed from
+    # an undefined band
+    f_d = torch.empty(1, dtype=torch.float64, device="cuda")
+    w, Th = case(64, 8, 100, 30.0, 1e-3, 10.0, 7)
+    for bad in (-1.0, float("nan"), float("inf")):
+        lam = w.lam.copy()
+        lam[17] = bad
+        got = noalloc(tomo, w.M, w.N, dev(lam), w.band_k, w.gamma, dev(w.P), dev(Th), f_d)
+        assert np.isnan(got), (bad, got)
+    # and a valid call right after is unaffected
+    with tomo.Plan.from_workload(w) as pl:
+        f_ref = pl.objective(dev(w.P), dev(Th))
+    got = noalloc(tomo, w.M, w.N, dev(w.lam), w.band_k, w.gamma, dev(w.P), dev(Th), f_d)
+    assert got == pytest.approx(f_ref, rel=REL)
