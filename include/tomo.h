@@ -138,8 +138,8 @@ typedef struct {
                               (checked with a double-precision residual) */
     int32_t max_newton;    /* 1000: Newton iterations, both stages together */
     int32_t max_stage1;    /* 200: stage-1 iterations */
-    int32_t max_cg;        /* 500: cap on Hessian products per Newton iteration
-                              (CG normally stops earlier on its forcing rule) */
+    int32_t max_cg;        /* 10000: cap on Hessian products per Newton iteration,
+                              a safety bound (CG stops on its forcing rule) */
     int32_t ls_max;        /* 50: backtracking steps per line search */
     int32_t start_stage;   /* 1: Algorithm 3; 2: stage 2 only (Algorithm 1) */
     int32_t warm_start;    /* 0: Theta^(0) = 1/N; 1: start from Theta as passed */

@@ -34,7 +34,8 @@
  *           stage's projection (simplex rows in stage 1, max(0,.) in stage 2).
  *   CG:     p0 = 0; stop when ||r|| <= eta ||b||, eta = min(eta_max,
  *           ||b||^eta_pow) (default min(0.5, sqrt(||b||))), or after max_cg
- *           (default 500) Hessian products; non-descent result ->
+ *           (default 10000, a safety bound: the forcing test is the working
+ *           rule) Hessian products; non-descent result ->
  *           p = -grad / diag.
  *   Armijo: accept the smallest m with f(x(beta^m)) <= f(x) + c grad^T
  *           (x(beta^m) - x) (projected-arc form), beta = 3/4, c = 1/10.
@@ -543,7 +544,7 @@ ORC_API void orc_default_opts(orc_opts *o)
     o->f_target = 0.0;
     o->max_newton = 1000;
     o->max_stage1 = 200;
-    o->max_cg = 500;
+    o->max_cg = 10000;
     o->ls_max = 50;
     o->start_stage = 1;
     o->warm_start = 0;

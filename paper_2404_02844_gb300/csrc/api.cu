@@ -541,7 +541,7 @@ void tomo_fit_opts_default(tomo_fit_opts *o)
     o->f_target = 0.0;
     o->max_newton = 1000;
     o->max_stage1 = 200;
-    o->max_cg = 500;
+    o->max_cg = 10000;
     o->ls_max = 50;
     o->start_stage = 1;
     o->warm_start = 0;

@@ -336,6 +336,53 @@ def test_c3_scale_products_on_sampled_rows(tomo):
         Xd = dev(X)
 
 
+def test_c3_scale_tensor_core_hvp_on_sampled_rows(tomo):
+    """The chosen form's Hessian product at the full megascale size (M = D =
+    1e6, N = 100, band +-10 sqrt(lambda), gamma = 1e-3): HV = 2 F^T F V +
+    2 gamma L V on the tensor cores, checked on sampled photon-number rows
+    against the oracle.  For a row i the oracle sums F_{d,i} (F V)_d over the
+    probes whose band holds i (Eq. Fmatrix; the products of Table ops), so
+    the rows exercise tiles with many split-K units (large lambda), the
+    vacuum end and the last row (no probe reaches it)."""
+    M, N, D = 1_000_000, 100, 1_000_000
+    gamma = 1e-3
+    lam = workloads.probe_intensities(D, 9e5)
+    rng = np.random.default_rng(17)
+    V = rng.standard_normal((M, N))
+    pr = oracle.Problem(M, N, lam, 10.0, gamma, store_F=False)
+    lo, hi = pr.bands()
+    rows_i = [0, 1, 7, 4999, 5000, 5001, 77777, 450000, M - 1]
+    with tomo.Plan(M, N, lam, 10.0, gamma, precision="tc") as pl:
+        Vd = dev(V)
+        HV = pl.hvp(Vd)
+        got = host(HV[torch.tensor(rows_i, device="cuda")])
+        HV2 = pl.hvp(Vd)
+        same = bool(torch.equal(HV, HV2))
+        del HV, HV2, Vd
+    assert same, "tensor-core product not deterministic"
+    Va = np.abs(V)
+    for k, i in enumerate(rows_i):
+        ds = np.nonzero((lo <= i) & (hi >= i))[0]
+        lap = np.zeros(N)
+        lap_s = np.zeros(N)
+        if i > 0:
+            lap += V[i] - V[i - 1]
+            lap_s += Va[i] + Va[i - 1]
+        if i < M - 1:
+            lap += V[i] - V[i + 1]
+            lap_s += Va[i] + Va[i + 1]
+        ref = 2.0 * gamma * lap
+        scale = 2.0 * gamma * lap_s
+        if len(ds):
+            wts = np.array([oracle.poisson(i, lam[d]) for d in ds])
+            ref = ref + 2.0 * wts @ pr.apply_F_rows(V, ds)
+            scale = scale + 2.0 * wts @ pr.apply_F_rows(Va, ds)
+        err = np.abs(got[k] - ref) / (scale + 1e-300)
+        assert err.max() <= TOLTC, (i, len(ds), err.max())
+    # no probe reaches the last photon number: only the smoothness term acts
+    assert not np.any((lo <= M - 1) & (hi >= M - 1))
+
+
 @pytest.mark.parametrize("prec", ["fp32", "tc"])
 def test_fit_batched_matches_single_and_oracle(tomo, prec):
     """Instances of the batched distribution (small M), each at the four

@@ -410,7 +410,7 @@ def test_fit_invariants_and_paper_constants_c1():
     assert np.all(np.diff(hist) <= 1e-15 * hist[:-1])  # Armijo: f never increases
     assert rep["kkt"] < 1e-10
     # soft check against the iteration counts the paper reports (its CG count
-    # per Newton step describes its own problem; here only the cap binds)
+    # per Newton step describes its own problem; the cap is a safety bound)
     assert rep["iters_s1"] <= 3 * gold["stage1_newton_iters"]["range"][1]
     assert rep["cg_total"] / max(1, rep["iters_s1"] + rep["iters_s2"]) <= o["max_cg"]
 

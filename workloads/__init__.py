@@ -216,17 +216,19 @@ def config_c4(n_instances=256, max_M=8192, shots=1_000_000):
     efficiency U[0.3, 0.95], D = 2M probes with lambda linear in [0, 0.75 M],
     1e6 shots; each to be solved at gamma in C4_GAMMAS.  Instance j uses seed
     BASE_SEED + 3 + 1000 j."""
-    out = []
-    for j in range(n_instances):
-        seed = BASE_SEED + 3 + 1000 * j
-        rng = np.random.Generator(np.random.PCG64(seed))
-        M = int(rng.integers(256, max_M + 1))
-        N = int(rng.integers(8, 129))
-        eta = float(rng.uniform(0.3, 0.95))
-        D = 2 * M
-        out.append(make_workload(f"c4_{j}_M{M}_N{N}", M, N - 1, eta, D, 0.75 * M, C4_GAMMAS[0],
-                                 10.0, shots, seed))
-    return out
+    return [config_c4_instance(j, max_M, shots) for j in range(n_instances)]
+
+
+def config_c4_instance(j, max_M=8192, shots=1_000_000):
+    """Instance j of config_c4 alone (same seed, same draws)."""
+    seed = BASE_SEED + 3 + 1000 * j
+    rng = np.random.Generator(np.random.PCG64(seed))
+    M = int(rng.integers(256, max_M + 1))
+    N = int(rng.integers(8, 129))
+    eta = float(rng.uniform(0.3, 0.95))
+    D = 2 * M
+    return make_workload(f"c4_{j}_M{M}_N{N}", M, N - 1, eta, D, 0.75 * M, C4_GAMMAS[0],
+                         10.0, shots, seed)
 
 
 def small_case(M=48, bins=7, eta=0.75, D=80, X=40.0, gamma=1e-3, band_k=10.0,
