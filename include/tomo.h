@@ -165,10 +165,11 @@ typedef struct {
                               line-search trials, host ms since the start,
                               trials rejected for a negative implicit entry
                               (stage 2), how CG ended: 0 forcing test,
-                              1 product cap, 2 non-positive curvature) */
+                              1 product cap, 2 non-positive curvature,
+                              host ms spent in the CG loop) */
 } tomo_fit_opts;
 
-#define TOMO_TRACE_COLS 10
+#define TOMO_TRACE_COLS 11
 
 /* Result of a fit. */
 typedef struct {

@@ -51,8 +51,8 @@ class tomo_fit_opts(ctypes.Structure):
                 ("cg_eta_max", c_dbl), ("cg_eta_pow", c_dbl), ("max_seconds", c_dbl),
                 ("trace", c_ptr)]
 
-TRACE_COLS = 10
-TRACE_NAMES = ("stage", "f", "kkt", "cg", "cg_rel_res", "alpha", "ls", "ms", "ls_neg", "cg_end")
+TRACE_COLS = 11
+TRACE_NAMES = ("stage", "f", "kkt", "cg", "cg_rel_res", "alpha", "ls", "ms", "ls_neg", "cg_end", "cg_ms")
 
 
 class tomo_fit_report(ctypes.Structure):

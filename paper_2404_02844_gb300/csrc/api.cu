@@ -727,12 +727,15 @@ static tomo_status cg_chunk(Plan &p, int stage, int count, const ChunkEvents *ev
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     if (evs) CUDA_TRY(cudaStreamIsCapturing(p.stream, &cap));
     const unsigned evflag = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0u;
+    // tensor-core form with N <= 128: the mirror of the product input is
+    // written by the previous direction update (or once after the set-up)
+    const bool fused_p = tc && tc_update_p_fusable(p);
     for (int c = 0; c < count; ++c) {
         if (evs) CUDA_TRY(cudaEventRecordWithFlags(evs->ev[c][0], p.stream, evflag));
         if (tc) {
             // tensor cores: the whole Hessian product (forward + adjoint) is
             // timed as the "forward" interval, the adjoint interval is empty
-            CUDA_TRY(launch_hvp_tc(p, in, p.q, p.cg_f32, true, stage));
+            CUDA_TRY(launch_hvp_tc(p, in, p.q, p.cg_f32, true, stage, !fused_p));
             if (evs) CUDA_TRY(cudaEventRecordWithFlags(evs->ev[c][1], p.stream, evflag));
         } else {
             CUDA_TRY(launch_forward(p, prec_products(p.precision), FWD_STORE, in, p.O, nullptr, true));
@@ -743,7 +746,8 @@ static tomo_status cg_chunk(Plan &p, int stage, int count, const ChunkEvents *ev
         // the tensor-core adjoint applies the restriction itself when it can
         if (!(tc && tc_restrict_fusable(p))) CUDA_TRY(launch_cg_restrict(p, stage));
         CUDA_TRY(launch_cg_update_xr(p, stage));
-        CUDA_TRY(launch_cg_update_p(p, stage));
+        if (fused_p) CUDA_TRY(launch_cg_update_p_split(p, stage));
+        else CUDA_TRY(launch_cg_update_p(p, stage));
     }
     return TOMO_OK;
 }
@@ -858,6 +862,10 @@ static tomo_status fit_impl(Plan &p, const double *P, const tomo_fit_opts &o, to
         if (stage == 1 && rep.iters_s1 >= o.max_stage1) stage = 2;
         CUDA_TRY(launch_setup1(p, stage, o.eps_bar));
         CUDA_TRY(launch_setup2(p, stage, o.max_cg, o.cg_eta_max, o.cg_eta_pow));
+        // the first Hessian product's input mirror (later ones come from the
+        // fused direction update)
+        if (hvp_on_tensor_cores(p.precision) && tc_update_p_fusable(p))
+            CUDA_TRY(launch_tc_split_input(p, stage == 1 ? p.p : p.u, p.cg_f32, true));
         TOMO_TRY(read_scalars(p));
         const double kkt = std::sqrt(p.sc_host->kkt2 / MN);
         if (!std::isfinite(kkt) || !std::isfinite(f))
@@ -872,6 +880,7 @@ static tomo_status fit_impl(Plan &p, const double *P, const tomo_fit_opts &o, to
             if (f <= o.f_target) { rep.stop = 1; break; }
         }
         // truncated Newton direction: PCG on the free variables
+        const double t_cg0 = trow ? elapsed_ms() : 0.0;
         int active = p.sc_host->cg_active;
         int done = 0;
         while (active) {
@@ -909,6 +918,7 @@ static tomo_status fit_impl(Plan &p, const double *P, const tomo_fit_opts &o, to
             trow[5] = 0.0;
             trow[6] = rep.ls_total;
             trow[9] = !(c.pq > 0.0) && c.cg_iters > 0 ? 2.0 : (c.cg_iters >= c.max_cg && !(std::sqrt(c.rr) <= c.tol)) ? 1.0 : 0.0;
+            trow[10] = elapsed_ms() - t_cg0;
         }
         CUDA_TRY(launch_direction(p, stage));
         if (stage == 1) ++rep.iters_s1; else ++rep.iters_s2;

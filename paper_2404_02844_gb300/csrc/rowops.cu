@@ -425,6 +425,69 @@ __global__ void k_cg_update_xr(RowArgs a, int stage, const uint8_t *freem, const
     });
 }
 
+// The same update for float vectors with N % 4 == 0, a float4 per lane: all
+// loads of a row are issued before any is used (one memory round trip per
+// row instead of one per 32 columns), and each lane sums its four values in
+// float before the per-row double accumulation.
+template <int CPL>
+__global__ void k_cg_update_xr_f4(RowArgs a, int stage, const uint8_t *freem, const float4 *p,
+                                  const float4 *q, float4 *x, float4 *r, float4 *z)
+{
+    if (a.sc->cg_active == 0) return;
+    const float alf = float(a.sc->alpha);
+    const int64_t nc = a.N / 4;
+    const uchar4 *fm4 = reinterpret_cast<const uchar4 *>(freem);
+    double rz = 0.0, rr = 0.0;
+    ROW_LOOP_BEGIN
+    const float inv = a.hinv[(stage == 1 ? 0 : a.M) + i];
+    float4 pv[CPL], qv[CPL], xv[CPL], rv[CPL];
+    uchar4 fv[CPL];
+#pragma unroll
+    for (int k = 0; k < CPL; ++k) {
+        const int64_t c = lane + 32 * k;
+        if (c < nc) {
+            const int64_t e = i * nc + c;
+            pv[k] = p[e];
+            qv[k] = q[e];
+            xv[k] = x[e];
+            rv[k] = r[e];
+            fv[k] = fm4[e];
+        }
+    }
+    float rz_row = 0.f, rr_row = 0.f;
+#pragma unroll
+    for (int k = 0; k < CPL; ++k) {
+        const int64_t c = lane + 32 * k;
+        if (c < nc) {
+            const int64_t e = i * nc + c;
+            float4 xo, ro, zo;
+            xo.x = fmaf(alf, pv[k].x, xv[k].x); ro.x = fmaf(-alf, qv[k].x, rv[k].x); zo.x = fv[k].x ? ro.x * inv : 0.f;
+            xo.y = fmaf(alf, pv[k].y, xv[k].y); ro.y = fmaf(-alf, qv[k].y, rv[k].y); zo.y = fv[k].y ? ro.y * inv : 0.f;
+            xo.z = fmaf(alf, pv[k].z, xv[k].z); ro.z = fmaf(-alf, qv[k].z, rv[k].z); zo.z = fv[k].z ? ro.z * inv : 0.f;
+            xo.w = fmaf(alf, pv[k].w, xv[k].w); ro.w = fmaf(-alf, qv[k].w, rv[k].w); zo.w = fv[k].w ? ro.w * inv : 0.f;
+            x[e] = xo;
+            r[e] = ro;
+            z[e] = zo;
+            rz_row = fmaf(ro.x, zo.x, rz_row); rz_row = fmaf(ro.y, zo.y, rz_row);
+            rz_row = fmaf(ro.z, zo.z, rz_row); rz_row = fmaf(ro.w, zo.w, rz_row);
+            rr_row = fmaf(ro.x, ro.x, rr_row); rr_row = fmaf(ro.y, ro.y, rr_row);
+            rr_row = fmaf(ro.z, ro.z, rr_row); rr_row = fmaf(ro.w, ro.w, rr_row);
+        }
+    }
+    rz += double(rz_row);
+    rr += double(rr_row);
+    ROW_LOOP_END
+    double v[2] = {rz, rr};
+    DevScalars *sc = a.sc;
+    grid_reduce<2>(v, a.partials, a.pstride, &sc->ticket[0], [sc](const double *t) {
+        sc->beta = t[0] / sc->rz;
+        sc->rz = t[0];
+        sc->rr = t[1];
+        sc->cg_iters += 1;
+        if (sqrt(t[1]) <= sc->tol || sc->cg_iters >= sc->max_cg) sc->cg_active = 0;
+    });
+}
+
 // p = z + beta p; stage 2 also u = E p.
 template <int VPL, typename VT>
 __global__ void k_cg_update_p(RowArgs a, int stage, const int32_t *mrow, const VT *z,
@@ -792,6 +855,18 @@ cudaError_t launch_cg_restrict(Plan &p, int stage)
 cudaError_t launch_cg_update_xr(Plan &p, int stage)
 {
     RowArgs a = row_args(p);
+    if (p.cg_f32 && (p.N % 4) == 0) {
+        auto f4 = [](double *b) { return reinterpret_cast<float4 *>(b); };
+        const int64_t cpl = (p.N / 4 + 31) / 32;
+        if (cpl <= 1)
+            k_cg_update_xr_f4<1><<<row_grid(p), ROW_WARPS * 32, 0, p.stream>>>(a, stage, p.freem, f4(p.p), f4(p.q), f4(p.x), f4(p.r), f4(p.z));
+        else if (cpl <= 2)
+            k_cg_update_xr_f4<2><<<row_grid(p), ROW_WARPS * 32, 0, p.stream>>>(a, stage, p.freem, f4(p.p), f4(p.q), f4(p.x), f4(p.r), f4(p.z));
+        else
+            k_cg_update_xr_f4<8><<<row_grid(p), ROW_WARPS * 32, 0, p.stream>>>(a, stage, p.freem, f4(p.p), f4(p.q), f4(p.x), f4(p.r), f4(p.z));
+        count_launch();
+        return cudaGetLastError();
+    }
     if (p.cg_f32)
         k_cg_update_xr<float><<<row_grid(p), ROW_WARPS * 32, 0, p.stream>>>(
             a, stage, p.freem, CGV(p.p), CGV(p.q), CGV(p.x), CGV(p.r), CGV(p.z));

@@ -728,6 +728,83 @@ __global__ void k_transpose_split(const int32_t *gate, int64_t M, int64_t N, con
 }
 
 // ----------------------------------------------------------------------------
+// CG direction update of the tensor-core form fused with the transposed split
+// of the next Hessian product's input: p = z + beta p (float vectors, N <= 128,
+// N % 4 == 0); stage 2 also lifts u = E p (column m(i) := -sum of the
+// others).  The product input (p in stage 1, u in stage 2) is written as the
+// transposed bf16 hi/lo mirror the forward contraction reads.  One CTA per 32
+// rows (a warp per row, a float4 per lane), the transposition through a
+// padded shared-memory tile.  Gated on the CG flag like the other CG kernels.
+// ----------------------------------------------------------------------------
+constexpr int UPS_ROWS = 32;
+
+__global__ void __launch_bounds__(256)
+k_cg_update_p_split(const int32_t *gate, const double *beta_p, int64_t M, int64_t N, int stage,
+                    const int32_t *mrow, const float *z, float *p, float *u,
+                    __nv_bfloat16 *t_hi, __nv_bfloat16 *t_lo, int64_t pitch)
+{
+    if (gate && *gate == 0) return;
+    __shared__ float tile[UPS_ROWS][128 + 1];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t i0 = int64_t(blockIdx.x) * UPS_ROWS;
+    const float be = float(*beta_p);
+    const int nc = int(N / 4);
+    for (int rr = warp; rr < UPS_ROWS; rr += 8) {
+        const int64_t i = i0 + rr;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (i < M) {
+            if (lane < nc) {
+                const float4 zv = reinterpret_cast<const float4 *>(z)[i * nc + lane];
+                const float4 pv = reinterpret_cast<const float4 *>(p)[i * nc + lane];
+                v.x = fmaf(be, pv.x, zv.x);
+                v.y = fmaf(be, pv.y, zv.y);
+                v.z = fmaf(be, pv.z, zv.z);
+                v.w = fmaf(be, pv.w, zv.w);
+                reinterpret_cast<float4 *>(p)[i * nc + lane] = v;
+            }
+            if (stage == 2) {
+                const int m = mrow[i];
+                float s = (v.x + v.y) + (v.z + v.w);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+                const float4 vm = make_float4(__shfl_sync(0xffffffffu, v.x, m >> 2),
+                                              __shfl_sync(0xffffffffu, v.y, m >> 2),
+                                              __shfl_sync(0xffffffffu, v.z, m >> 2),
+                                              __shfl_sync(0xffffffffu, v.w, m >> 2));
+                const float pm = (m & 3) == 0 ? vm.x : (m & 3) == 1 ? vm.y : (m & 3) == 2 ? vm.z : vm.w;
+                const float lift = -(s - pm);
+                if (lane == (m >> 2)) {
+                    if ((m & 3) == 0) v.x = lift;
+                    else if ((m & 3) == 1) v.y = lift;
+                    else if ((m & 3) == 2) v.z = lift;
+                    else v.w = lift;
+                }
+                if (lane < nc) reinterpret_cast<float4 *>(u)[i * nc + lane] = v;
+            }
+        }
+        if (lane < 32) {
+            float *t = &tile[rr][4 * lane];
+            t[0] = v.x; t[1] = v.y; t[2] = v.z; t[3] = v.w;
+        }
+    }
+    __syncthreads();
+    // chunk (n, j): photon numbers i0 + 8 j .. + 7 of outcome n, one 16-byte
+    // copy of each part; rows beyond M hold zeros (the mirror's padding)
+    for (int c = tid; c < int(N) * (UPS_ROWS / 8); c += 256) {
+        const int n = c / (UPS_ROWS / 8), j = c % (UPS_ROWS / 8);
+        const int64_t row0 = i0 + 8 * j;
+        if (row0 >= M) continue;
+        float v8[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) v8[t] = tile[8 * j + t][n];
+        uint4 hi, lo;
+        split_pack(v8, hi, lo);
+        *reinterpret_cast<uint4 *>(t_hi + n * pitch + row0) = hi;
+        *reinterpret_cast<uint4 *>(t_lo + n * pitch + row0) = lo;
+    }
+}
+
+// ----------------------------------------------------------------------------
 // launchers
 // ----------------------------------------------------------------------------
 template <int BN, int SPLIT, bool FWD>
@@ -797,7 +874,7 @@ bool tc_restrict_fusable(const Plan &p)
     return p.cg_f32 && band_bn(p.N) >= p.N && (p.N % 4) == 0;
 }
 
-cudaError_t launch_hvp_tc(Plan &p, const void *V, void *HV, bool vec_f32, bool gated, int restrict_stage)
+cudaError_t launch_tc_split_input(Plan &p, const void *V, bool vec_f32, bool gated)
 {
     const int32_t *gate = gated ? &p.sc->cg_active : nullptr;
     dim3 tb(32, 8), tg(unsigned((p.M + 31) / 32), unsigned((p.N + 31) / 32));
@@ -808,8 +885,30 @@ cudaError_t launch_hvp_tc(Plan &p, const void *V, void *HV, bool vec_f32, bool g
         k_transpose_split<double><<<tg, tb, 0, p.stream>>>(gate, p.M, p.N, static_cast<const double *>(V),
                                                             p.ut_hi, p.ut_lo, p.ut_pitch);
     count_launch();
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+bool tc_update_p_fusable(const Plan &p)
+{
+    return tc_restrict_fusable(p) && p.N <= 128;
+}
+
+cudaError_t launch_cg_update_p_split(Plan &p, int stage)
+{
+    float *pf = reinterpret_cast<float *>(p.p), *uf = reinterpret_cast<float *>(p.u);
+    k_cg_update_p_split<<<unsigned((p.M + UPS_ROWS - 1) / UPS_ROWS), 256, 0, p.stream>>>(
+        &p.sc->cg_active, &p.sc->beta, p.M, p.N, stage, p.mrow, reinterpret_cast<const float *>(p.z), pf, uf,
+        p.ut_hi, p.ut_lo, p.ut_pitch);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hvp_tc(Plan &p, const void *V, void *HV, bool vec_f32, bool gated, int restrict_stage,
+                          bool split_input)
+{
+    const int32_t *gate = gated ? &p.sc->cg_active : nullptr;
+    cudaError_t e;
+    if (split_input && (e = launch_tc_split_input(p, V, vec_f32, gated)) != cudaSuccess) return e;
     TcArgs f = tc_args(p, true, gate);
     if ((e = launch_tc<true>(p, f)) != cudaSuccess) return e;
     TcArgs b = tc_args(p, false, gate);

@@ -186,8 +186,17 @@ inline bool hvp_on_tensor_cores(int precision) { return precision == TOMO_PREC_T
 // V, HV: float when vec_f32 (the CG vectors of the tensor-core form), else double
 // restrict_stage 1 or 2 also applies the CG restriction of that stage to HV
 // and finishes p^T q and alpha (float vectors, when tc_restrict_fusable)
-cudaError_t launch_hvp_tc(Plan &p, const void *V, void *HV, bool vec_f32, bool gated, int restrict_stage = 0);
+// split_input = false: the transposed bf16 mirror of V is already current
+// (written by launch_cg_update_p_split or launch_tc_split_input)
+cudaError_t launch_hvp_tc(Plan &p, const void *V, void *HV, bool vec_f32, bool gated, int restrict_stage = 0,
+                          bool split_input = true);
 bool tc_restrict_fusable(const Plan &p);
+// the transposed bf16 hi/lo mirror of a product input V (M x N, float or double)
+cudaError_t launch_tc_split_input(Plan &p, const void *V, bool vec_f32, bool gated);
+// CG direction update p = z + beta p (and u = E p in stage 2) fused with the
+// mirror of the next product's input; float CG vectors, N <= 128, N % 4 == 0
+bool tc_update_p_fusable(const Plan &p);
+cudaError_t launch_cg_update_p_split(Plan &p, int stage);
 cudaError_t launch_hvp_tc_wait_selftest(Plan &p, const double *V, double *HV);
 size_t tc_smem_bytes(int bn);
 
