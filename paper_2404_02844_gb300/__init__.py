@@ -114,6 +114,8 @@ EXPORTS = [
     ("tomo_ws_train_step", c_i32, [c_ptr, c_ptr, c_ptr, c_ptr, c_i32, ctypes.c_float,
                                    ctypes.POINTER(ctypes.c_float)]),
     ("tomo_ws_infer", c_i32, [c_ptr, c_ptr, c_i64, c_ptr]),
+    ("tomo_fit_warm", c_i32, [c_ptr, c_ptr, c_ptr, c_ptr, ctypes.POINTER(tomo_fit_opts),
+                              ctypes.POINTER(tomo_fit_report), ctypes.POINTER(c_i32)]),
     ("tomo_ws_save", c_i32, [c_ptr, ctypes.c_char_p]),
     ("tomo_ws_load", c_i32, [c_ptr, ctypes.c_char_p]),
     ("tomo_kernel_launches", c_i64, []),
@@ -539,19 +541,25 @@ class WarmStart:
 
 
 def fit_warm(plan, ws, P, **opts):
-    """Algorithm 3 started from the learned Theta0, falling back to 1/N when
-    f(Theta0) >= f(1/N) or when the warm-started fit fails.  Returns (Theta,
+    """tomo_fit_warm: Algorithm 3 started from the learned Theta0, falling
+    back to 1/N when f(Theta0) >= f(1/N) or when the warm-started fit fails
+    (the rule runs in the library).  P: float64 CUDA tensor.  Returns (Theta,
     report, used_warm_start)."""
     import torch
-    Th0 = ws.infer(P)
-    uni = torch.full_like(Th0, 1.0 / Th0.shape[1])
-    use = plan.objective(P, Th0) < plan.objective(P, uni)
-    if use:
-        Th, rep = plan.fit(P, Th0, **opts)
-        if rep["status"] in ("TOMO_OK", "TOMO_ENOTCONV") and np.isfinite(rep["f"]):
-            return Th, rep, True
-    Th, rep = plan.fit(P, **opts)
-    return Th, rep, False
+    o = tomo_fit_opts_default()
+    for k, v in opts.items():
+        if not hasattr(o, k) or k in ("trace", "trace_len"):
+            raise KeyError(k)
+        setattr(o, k, v)
+    Th = torch.empty(plan.M, plan.N, dtype=torch.float64, device="cuda")
+    rep = tomo_fit_report()
+    used = c_i32(0)
+    st = lib().tomo_fit_warm(plan._h, ws._h, _ptr(P), _ptr(Th), ctypes.byref(o), ctypes.byref(rep),
+                             ctypes.byref(used))
+    _check(st, "tomo_fit_warm", allow=(0, 4))
+    d = _fit_dict(rep)
+    d["status"] = STATUS[st]
+    return Th, d, bool(used.value)
 
 
 def plan_tc_units(st, en, align=64, max_unit=1024, ctas=152):

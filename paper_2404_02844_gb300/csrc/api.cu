@@ -215,6 +215,29 @@ static void plan_tc_units(const int64_t *st, const int64_t *en, int tiles, int a
     }
 }
 
+// Host planning for many tiles (at least 8 per CTA): whole tiles dealt to the
+// CTAs round-robin, tile t to CTA t mod ctas, in tile order.  Every tile is
+// one unit (no split-K partial), neighbouring tiles (whose reduction ranges
+// overlap) run at the same time on different SMs and share their vector
+// operand in L2, and the CTAs' sums of tile lengths are close because the
+// lengths change slowly from tile to tile.
+static void plan_tc_tiles_rr(const int64_t *st, const int64_t *en, int tiles, int64_t ctas,
+                             std::vector<WorkUnit> &units, std::vector<int32_t> &cta_first,
+                             std::vector<int32_t> &nsplit)
+{
+    if (ctas < 1) ctas = 1;
+    units.clear();
+    cta_first.assign(1, 0);
+    nsplit.assign(tiles, 1);
+    for (int64_t c = 0; c < ctas && c < tiles; ++c) {
+        for (int64_t t = c; t < tiles; t += ctas) {
+            const bool empty = en[t] <= st[t];
+            units.push_back(WorkUnit{int32_t(t), 0, empty ? 0 : int32_t(st[t]), empty ? 0 : int32_t(en[t])});
+        }
+        cta_first.push_back(int32_t(units.size()));
+    }
+}
+
 // Tensor-core schedule, one wave of persistent CTAs: the reduction ranges of
 // all tiles, laid end to end, are cut into `ctas` shares of equal length
 // (multiples of `align`); a share that crosses a tile boundary becomes one
@@ -231,7 +254,10 @@ static cudaError_t make_schedule_tc(Plan &p, Schedule &S, const std::vector<int6
     const int64_t ncol = (p.N + bn - 1) / bn;
     std::vector<WorkUnit> units;
     std::vector<int32_t> cta_first, nsplit, first(tiles, 0);
-    plan_tc_units(st.data(), en.data(), tiles, align, max_unit, ctas, units, cta_first, nsplit);
+    if (int64_t(tiles) >= 8 * ctas)
+        plan_tc_tiles_rr(st.data(), en.data(), tiles, ctas, units, cta_first, nsplit);
+    else
+        plan_tc_units(st.data(), en.data(), tiles, align, max_unit, ctas, units, cta_first, nsplit);
     // every unit writes a partial tile (the finish kernel combines them)
     int64_t slots = 0;
     for (int t = 0; t < tiles; ++t) { first[t] = int32_t(slots); slots += nsplit[t]; }
@@ -241,15 +267,13 @@ static cudaError_t make_schedule_tc(Plan &p, Schedule &S, const std::vector<int6
     if ((e = dalloc(&S.units, int64_t(units.size())))) return e;
     if ((e = dalloc(&S.tile_first, tiles))) return e;
     if ((e = dalloc(&S.tile_nsplit, tiles))) return e;
-    if ((e = dalloc(&S.counters, tiles * ncol))) return e;
     if ((e = dalloc(&S.cta_first, int64_t(cta_first.size())))) return e;
     if ((e = cudaMalloc(&S.part, std::max<int64_t>(1, slots * ncol) * TILE_R * bn * sizeof(float)))) return e;
     if ((e = cudaMemcpyAsync(S.units, units.data(), sizeof(WorkUnit) * units.size(), cudaMemcpyHostToDevice, p.stream)) ||
         (e = cudaMemcpyAsync(S.tile_first, first.data(), sizeof(int32_t) * tiles, cudaMemcpyHostToDevice, p.stream)) ||
         (e = cudaMemcpyAsync(S.tile_nsplit, nsplit.data(), sizeof(int32_t) * tiles, cudaMemcpyHostToDevice, p.stream)) ||
         (e = cudaMemcpyAsync(S.cta_first, cta_first.data(), sizeof(int32_t) * cta_first.size(),
-                             cudaMemcpyHostToDevice, p.stream)) ||
-        (e = cudaMemsetAsync(S.counters, 0, sizeof(unsigned) * tiles * ncol, p.stream)))
+                             cudaMemcpyHostToDevice, p.stream)))
         return e;
     // the finish kernel's grid reduction: one partial per (32-row slice, column block)
     *max_ctas = std::max<int64_t>(*max_ctas, std::max<int64_t>(S.n_ctas, tiles * (TILE_R / 32)) * ncol);
@@ -378,6 +402,12 @@ static cudaError_t build_schedules(Plan &p, bool tensor_cores)
                 return e;
             if ((e = cudaMemsetAsync(p.ut_hi, 0, ub, p.stream)) || (e = cudaMemsetAsync(p.ut_lo, 0, ub, p.stream)) ||
                 (e = cudaMemsetAsync(p.ot_hi, 0, ob, p.stream)) || (e = cudaMemsetAsync(p.ot_lo, 0, ob, p.stream)))
+                return e;
+            const int bn = band_bn(p.N);
+            if ((e = encode_operand_map(&p.tm_ut_hi, p.ut_hi, p.ut_pitch, npad, bn)) ||
+                (e = encode_operand_map(&p.tm_ut_lo, p.ut_lo, p.ut_pitch, npad, bn)) ||
+                (e = encode_operand_map(&p.tm_ot_hi, p.ot_hi, p.ot_pitch, npad, bn)) ||
+                (e = encode_operand_map(&p.tm_ot_lo, p.ot_lo, p.ot_pitch, npad, bn)))
                 return e;
         }
     }
@@ -1031,6 +1061,43 @@ tomo_status tomo_fit(tomo_plan_t plan, const double *P, double *Theta, const tom
     rep.kernels = int32_t(tomo_kernel_launches() - l0);
     if (report) *report = rep;
     return rep.stop == 2 ? TOMO_ENOTCONV : TOMO_OK;
+}
+
+tomo_status tomo_fit_warm(tomo_plan_t plan, tomo_ws_t ws, const double *P, double *Theta,
+                          const tomo_fit_opts *opts, tomo_fit_report *report, int32_t *used_warm)
+{
+    Plan *pp = reinterpret_cast<Plan *>(plan);
+    if (used_warm) *used_warm = 0;
+    if (!pp || !ws || !P || !Theta) return fail(TOMO_EINVAL, "NULL argument");
+    Plan &p = *pp;
+    int64_t wD = 0, wM = 0, wC0 = 0;
+    if (!ws_shape(ws, &wD, &wM, &wC0) || wD != p.D || wM != p.M || p.N > wC0)
+        return fail(TOMO_EINVAL, "the warm-start handle does not match the plan (D, M, N <= C0)");
+    if (!is_device_pointer(P) || !is_device_pointer(Theta))
+        return fail(TOMO_EINVAL, "P and Theta must be device pointers");
+    tomo_fit_opts o;
+    if (opts) o = *opts; else tomo_fit_opts_default(&o);
+    const int64_t MN = p.M * p.N;
+    // Theta0 from the network, then f(Theta0) and f(1/N) in double
+    TOMO_TRY(tomo_ws_infer(ws, P, p.N, Theta));
+    double f0 = 0.0, fu = 0.0;
+    TOMO_TRY(residual_objective(p, P, Theta, p.R, &f0));
+    CUDA_TRY(launch_fill(p, p.Th, 1.0 / double(p.N), MN));
+    TOMO_TRY(residual_objective(p, P, p.Th, p.R, &fu));
+    if (std::isfinite(f0) && f0 < fu) {
+        o.warm_start = 1;
+        tomo_fit_report rep;
+        std::memset(&rep, 0, sizeof(rep));
+        const tomo_status st = tomo_fit(plan, P, Theta, &o, &rep);
+        if ((st == TOMO_OK || st == TOMO_ENOTCONV) && std::isfinite(rep.f)) {
+            if (report) *report = rep;
+            if (used_warm) *used_warm = 1;
+            return st;
+        }
+    }
+    // Theta0 no better than the uniform start, or the warm fit failed
+    o.warm_start = 0;
+    return tomo_fit(plan, P, Theta, &o, report);
 }
 
 tomo_status tomo_fit_batched(const tomo_desc *descs, const double *const *P, double *const *Theta,

@@ -11,16 +11,30 @@
 // accumulator is f32 in tensor memory.  Precision is recovered by splitting
 // every operand into hi + lo bf16 parts and accumulating hi*hi + hi*lo +
 // lo*hi (three MMAs per K slice, ~17 significant bits: the dropped lo*lo
-// term is of the order of what the two-part split itself leaves, 2^-18).  The weights F are generated
-// by all 256 threads straight into the swizzled A tile (runs of 8 photon
-// numbers from the log-space anchors, exact ratio recurrence in float); the
-// vector operand comes from a transposed bf16 hi/lo copy (rows = outcomes,
-// contiguous along the reduction index) so that one 16-byte load is one
-// swizzle chunk.  A single thread issues the MMAs of a stage and commits them
-// to the stage's mbarrier while the other threads already produce the next
-// stage (two stages).  The reduction range of every tile is cut into work
-// units (split-K, planned on the host); every unit writes its f32 partial
-// tile and a finish kernel sums each tile's partials in unit order.
+// term is of the order of what the two-part split itself leaves, 2^-18).
+//
+// The contraction kernel is warp-specialised and persistent (one CTA per SM,
+// a list of work units each):
+//   producer warps 0-7  generate the Poisson weights of every 64-wide slice
+//                       straight into a ring of A stages (runs of 8 photon
+//                       numbers from the log-space anchors, exact ratio
+//                       recurrence in float) and signal them on an mbarrier;
+//   warp 8              loads the vector operand of each slice by TMA from a
+//                       transposed bf16 hi/lo copy (rows = outcomes,
+//                       contiguous along the reduction index), issues the
+//                       slice's MMAs into one of two tensor-memory
+//                       accumulators and commits them to the barriers that
+//                       free the stages and publish a finished unit;
+//   warps 9-12          move each finished accumulator to the unit's f32
+//                       partial tile (column-major, coalesced stores) while
+//                       the MMAs of the next unit run in the other one.
+// The reduction range of every tile is cut into work units (split-K, planned
+// on the host); a finish kernel sums each tile's partials in unit order and
+// runs the epilogue.  Every mbarrier wait is bounded: a role that gives up
+// raises a CTA-wide abort flag, the others leave their loops, copies and MMAs
+// in flight are drained (bounded) and the host sees TOMO_ETIMEOUT.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -31,33 +45,41 @@
 
 namespace tomo {
 
-constexpr int TC_BK = 64;       // reduction slice per stage (one 128-byte bf16 row)
-constexpr int TC_STAGES = 2;      // A (weight) stages; the MMA barriers follow them
-constexpr int TC_BSTAGES = 3;     // B (vector) stages: B is copied one step ahead
-constexpr int TC_THREADS = 256;
+constexpr int TC_BK = 64;            // reduction slice per stage (one 128-byte bf16 row)
+constexpr int TC_SA = 3;             // A (weight) stages
+constexpr int TC_SB = 3;             // B (vector) stages, filled by TMA
+constexpr int TC_PROD = 256;         // producer threads (warps 0-7)
+constexpr int TC_MMA_WARP = 8;
+constexpr int TC_THREADS = 13 * 32;
 constexpr uint32_t TC_WAIT_LIMIT = 1u << 24;
+constexpr int TC_WIN = 3;            // windows of the per-slice tables (loaded two slices ahead)
+static_assert(TC_SA == TC_SB, "the B copy of slice g + 2 reuses the stage of slice g - 1");
 
-template <int BN, int SPLIT>
+template <int BN>
 struct TcLayout {
-    static constexpr int NPART = SPLIT == 3 ? 2 : 1;                 // hi (+ lo)
-    static constexpr int A_BYTES = TILE_R * TC_BK * 2;               // 16 KB
+    static constexpr int A_BYTES = TILE_R * TC_BK * 2;               // 16 KB, one bf16 part
     static constexpr int B_BYTES = BN * TC_BK * 2;
-    static constexpr int A_STAGE = NPART * A_BYTES;
-    static constexpr int B_STAGE = NPART * B_BYTES;
-    static constexpr int STAGE_BYTES = TC_STAGES * A_STAGE + TC_BSTAGES * B_STAGE;  // all stages
-    static constexpr int STAGING_BYTES = (TC_THREADS / 8) * 8 * 9 * 4;  // 8x8 transposes (+pad)
-    static constexpr int CTRL_BYTES = 64;
-    // per-unit tables: probe metadata (adjoint) and the 1/(i+1) pairs
-    static constexpr int META_BYTES = TC_MAX_UNIT * 24;
-    static constexpr int RINV_BYTES = (TC_MAX_UNIT + 2 * RUN + TILE_R) * 8;
-    static constexpr int TOTAL = 1024 + STAGE_BYTES + STAGING_BYTES + CTRL_BYTES +
-                                 META_BYTES + RINV_BYTES;
-    static constexpr int TMEM_COLS = BN < 32 ? 32 : BN;
+    static constexpr int A_STAGE = 2 * A_BYTES;                      // hi + lo
+    static constexpr int B_STAGE = 2 * B_BYTES;
+    static constexpr int B_OFF = TC_SA * A_STAGE;
+    static constexpr int STG_OFF = B_OFF + TC_SB * B_STAGE;
+    static constexpr int STAGING_BYTES = (TC_PROD / 8) * 8 * 9 * 4;  // 8x8 transposes (+pad)
+    static constexpr int TAB_OFF = STG_OFF + STAGING_BYTES;          // per-slice tables
+    static constexpr int TAB_BYTES = TC_WIN * TC_BK * (8 + 24) + (TILE_R + RUN) * 8;
+    static constexpr int BAR_OFF = TAB_OFF + TAB_BYTES;
+    static constexpr int NBARS = 2 * TC_SA + TC_SB + 4;              // a_full, a_empty, b_full, acc_full[2], acc_empty[2]
+    static constexpr int CTRL_BYTES = NBARS * 8 + 16;                // + tensor-memory holder, abort flag
+    static constexpr int TOTAL = 1024 + BAR_OFF + CTRL_BYTES;
+    static constexpr int ACC_COLS = BN < 32 ? 32 : BN;               // one accumulator
+    static constexpr int TMEM_COLS = 2 * ACC_COLS;                   // two (power of two >= 32)
     static_assert(TOTAL <= 227 * 1024, "shared memory per CTA");
-    static_assert(TILE_R * (BN + 1) * 4 + TILE_R * 4 <= STAGE_BYTES, "epilogue tile and row values fit the stage buffers");
+    static_assert(B_OFF % 1024 == 0 && B_STAGE % 1024 == 0 && B_BYTES % 1024 == 0, "swizzle atoms");
 };
 
 struct TcArgs {
+    // operand B: tensor maps of the transposed bf16 hi/lo copies (rows =
+    // outcomes, pitch bpitch, box 64 x BN, 128-byte swizzle)
+    CUtensorMap tm_b_hi, tm_b_lo;
     int64_t M, N, D;
     const float2 *lam2;
     const int32_t *lo, *hi;
@@ -68,11 +90,9 @@ struct TcArgs {
     const int32_t *cta_first;     // units of CTA c: cta_first[c] .. cta_first[c+1]-1
     const int32_t *tile_first;
     const int32_t *tile_nsplit;
-    unsigned int *counters;
     float *part;
     const int32_t *gate;
     int32_t *err;                 // set to 1 if a bounded wait gave up
-    // operand B: transposed bf16 hi/lo copy, rows = outcomes, pitch bpitch
     const __nv_bfloat16 *b_hi, *b_lo;
     int64_t bpitch;
     // forward output: transposed bf16 hi/lo copy of O (pitch opitch)
@@ -102,27 +122,6 @@ struct TcArgs {
     int skip_mma;
 };
 
-// Float weights of the run of 8 photon numbers i_r.. of probe d (zero outside
-// the band); same recurrence as the float SIMT contraction.
-__device__ __forceinline__ void tc_gen_run(const TcArgs &a, int64_t d, int64_t i_r, float (&v8)[RUN])
-{
-#pragma unroll
-    for (int t = 0; t < RUN; ++t) v8[t] = 0.f;
-    if (d >= a.D) return;
-    const int64_t lo = a.lo[d], hi = a.hi[d];
-    if (i_r + RUN - 1 < lo || i_r > hi) return;
-    const int64_t a0 = lo & ~int64_t(RUN - 1);
-    float v = a.anchor[a.aoff[d] + (i_r - a0) / RUN];
-    const float2 lam = a.lam2[d];
-#pragma unroll
-    for (int t = 0; t < RUN; ++t) {
-        const int64_t i = i_r + t;
-        v8[t] = (i >= lo && i <= hi) ? v : 0.f;
-        const float2 r = a.rinv2[i + 1];
-        v = v * fmaf(lam.x, r.x, fmaf(lam.x, r.y, lam.y * r.x));
-    }
-}
-
 struct ProbeMeta {
     int32_t lo, hi;     // band (lo > hi: empty)
     int64_t aoff;       // first anchor of the probe
@@ -133,10 +132,10 @@ __device__ __forceinline__ ProbeMeta load_meta(const TcArgs &a, int64_t d)
 {
     ProbeMeta m;
     if (d < a.D) {
-        m.lo = a.lo[d];
-        m.hi = a.hi[d];
-        m.aoff = a.aoff[d];
-        m.lam = a.lam2[d];
+        m.lo = __ldg(&a.lo[d]);
+        m.hi = __ldg(&a.hi[d]);
+        m.aoff = __ldg(&a.aoff[d]);
+        m.lam = __ldg(&a.lam2[d]);
     } else {
         m.lo = 1;
         m.hi = 0;
@@ -144,25 +143,6 @@ __device__ __forceinline__ ProbeMeta load_meta(const TcArgs &a, int64_t d)
         m.lam = make_float2(0.f, 0.f);
     }
     return m;
-}
-
-// Same run as tc_gen_run, from the probe's metadata and a shared-memory slice
-// of the 1/(i+1) pairs (rs[i - rbase] = 1/(i+1)).
-__device__ __forceinline__ void tc_gen_run_tbl(const float *anchor, const ProbeMeta &m, int64_t i_r,
-                                               const float2 *rs, int64_t rbase, float (&v8)[RUN])
-{
-#pragma unroll
-    for (int t = 0; t < RUN; ++t) v8[t] = 0.f;
-    if (i_r + RUN - 1 < m.lo || i_r > m.hi) return;
-    const int64_t a0 = int64_t(m.lo) & ~int64_t(RUN - 1);
-    float v = anchor[m.aoff + (i_r - a0) / RUN];
-#pragma unroll
-    for (int t = 0; t < RUN; ++t) {
-        const int64_t i = i_r + t;
-        v8[t] = (i >= m.lo && i <= m.hi) ? v : 0.f;
-        const float2 r = rs[i - rbase];
-        v = v * fmaf(m.lam.x, r.x, fmaf(m.lam.x, r.y, m.lam.y * r.x));
-    }
 }
 
 // Anchor of the run i_r.. of a probe, or 0 when the run misses the band.
@@ -173,35 +153,48 @@ __device__ __forceinline__ float anchor_of(const float *anchor, const ProbeMeta 
     return __ldg(&anchor[m.aoff + (i_r - a0) / RUN]);
 }
 
-// The run expanded from an anchor value already in a register.
-__device__ __forceinline__ void tc_expand_run(float v, const ProbeMeta &m, int64_t i_r, const float2 *rs,
-                                              int64_t rbase, float (&v8)[RUN])
+// The run of 8 photon numbers i_r.. of a probe expanded from its anchor v
+// (F at photon number i_r) with the exact ratio F_{i+1}/F_i = lambda / (i+1):
+// lambda and rs[t] = 1/(i_r + t + 1) are compensated float pairs (hi + lo;
+// the table is 16-byte aligned shared memory), so every ratio is the float
+// rounding of the exact one and a run carries at most 8 roundings -- the
+// same weights, bit for bit, in the forward and the adjoint contraction, and
+// within float rounding of the SIMT contractions that give the gradient.
+// Weights outside the band [lo, hi] are zero (checked per element only for
+// runs that cross a band edge).
+__device__ __forceinline__ void tc_expand_run(float v, float2 lam, int32_t lo, int32_t hi, int32_t i_r,
+                                              const float2 *rs, float (&v8)[RUN])
 {
+    float q[RUN - 1];
 #pragma unroll
-    for (int t = 0; t < RUN; ++t) {
-        const int64_t i = i_r + t;
-        v8[t] = (i >= m.lo && i <= m.hi) ? v : 0.f;
-        const float2 r = rs[i - rbase];
-        v = v * fmaf(m.lam.x, r.x, fmaf(m.lam.x, r.y, m.lam.y * r.x));
+    for (int t = 0; t < RUN - 1; t += 2) {
+        const float4 r = *reinterpret_cast<const float4 *>(rs + t);      // pairs t, t + 1
+        q[t] = fmaf(lam.x, r.x, fmaf(lam.x, r.y, lam.y * r.x));
+        if (t + 1 < RUN - 1) q[t + 1] = fmaf(lam.x, r.z, fmaf(lam.x, r.w, lam.y * r.z));
+    }
+    v8[0] = v;
+#pragma unroll
+    for (int t = 1; t < RUN; ++t) v8[t] = v8[t - 1] * q[t - 1];
+    if (i_r < lo || i_r + RUN - 1 > hi) {
+#pragma unroll
+        for (int t = 0; t < RUN; ++t)
+            if (i_r + t < lo || i_r + t > hi) v8[t] = 0.f;
     }
 }
 
-// 16-byte asynchronous global -> shared copy
-__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc)
+// Barrier of the 256 producer threads (named barrier 1) that also returns
+// the OR of their flags: every producer reaches it once per slice after
+// bounded waits only, so it cannot hold a producer forever.
+__device__ __forceinline__ bool producers_sync_or(bool v)
 {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(tc::smem_u32(smem_dst)), "l"(gsrc) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit()
-{
-    asm volatile("cp.async.commit_group;" ::: "memory");
-}
-__device__ __forceinline__ void cp_async_wait_group1()
-{
-    asm volatile("cp.async.wait_group 1;" ::: "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all()
-{
-    asm volatile("cp.async.wait_all;" ::: "memory");
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred pi, po;\n\t"
+        "setp.ne.u32 pi, %1, 0;\n\t"
+        "bar.red.or.pred po, 1, 256, pi;\n\t"
+        "selp.u32 %0, 1, 0, po;\n\t}"
+        : "=r"(r) : "r"(uint32_t(v)) : "memory");
+    return r != 0;
 }
 
 // Packs 8 floats into hi and lo bf16 chunks (hi = rn(v), lo = rn(v - hi)),
@@ -221,276 +214,327 @@ __device__ __forceinline__ void split_pack(const float (&v)[8], uint4 &hi, uint4
     lo = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
-template <int BN, int SPLIT, bool FWD>
-__global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(TcArgs a)
+// A bounded wait observed by a whole warp: every lane polls, the warp gives
+// up if any lane did (so the warp's control flow stays uniform).
+__device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, uint32_t limit, const volatile int *abort)
 {
-    using L = TcLayout<BN, SPLIT>;
+    const bool ok = tc::mbar_wait_or_abort(bar, parity, limit, abort);
+    return __all_sync(0xffffffffu, ok);
+}
+
+template <int BN, bool FWD>
+__global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(const __grid_constant__ TcArgs a)
+{
+    using L = TcLayout<BN>;
     if (a.gate && *a.gate == 0) return;
 
     extern __shared__ unsigned char tc_raw[];
     const uint32_t raw_u32 = tc::smem_u32(tc_raw);
     unsigned char *sm = tc_raw + (((raw_u32 + 1023u) & ~1023u) - raw_u32);
-    float *staging = reinterpret_cast<float *>(sm + L::STAGE_BYTES);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + L::STAGE_BYTES + L::STAGING_BYTES);
-    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + TC_STAGES);
-    ProbeMeta *meta_s = reinterpret_cast<ProbeMeta *>(sm + L::STAGE_BYTES + L::STAGING_BYTES +
-                                                      L::CTRL_BYTES);
-    float2 *rinv_s = reinterpret_cast<float2 *>(reinterpret_cast<unsigned char *>(meta_s) + L::META_BYTES);
+    float *staging = reinterpret_cast<float *>(sm + L::STG_OFF);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + L::BAR_OFF);
+    uint64_t *a_full = bars, *a_empty = bars + TC_SA, *b_full = bars + 2 * TC_SA;
+    uint64_t *acc_full = bars + 2 * TC_SA + TC_SB, *acc_empty = acc_full + 2;
+    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + L::NBARS);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_holder + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (warp == 0) {
         tc::tmem_alloc(tmem_holder, L::TMEM_COLS);
         tc::tmem_relinquish();
     }
-    if (tid == 0) {
-        for (int s = 0; s < TC_STAGES; ++s) tc::mbar_init(&bars[s], 1);
+    if (tid == TC_MMA_WARP * 32) {
+        for (int s = 0; s < TC_SA; ++s) {
+            tc::mbar_init(&a_full[s], TC_PROD / 32);   // one arrival per producer warp
+            tc::mbar_init(&a_empty[s], 1);             // MMA commit
+        }
+        for (int s = 0; s < TC_SB; ++s) tc::mbar_init(&b_full[s], 1);   // expect_tx arrival
+        for (int s = 0; s < 2; ++s) {
+            tc::mbar_init(&acc_full[s], 1);            // MMA commit
+            tc::mbar_init(&acc_empty[s], 4);           // one arrival per epilogue warp
+        }
+        *abort_flag = 0;
         tc::mbar_fence_init();
+        tc::tma_prefetch_desc(&a.tm_b_hi);
+        tc::tma_prefetch_desc(&a.tm_b_lo);
     }
     tc::tc_fence_before_sync();
     __syncthreads();
     tc::tc_fence_after_sync();
     const uint32_t tmem = *tmem_holder;
     const int64_t n0 = int64_t(blockIdx.y) * BN;
-    bool ok = true;
-    // pipeline steps issued by this CTA so far (stage and mbarrier phase of
-    // every step follow from it across units), and the last step whose MMAs
-    // were committed (-1: none), known to every thread
-    uint32_t gstep = 0;
-    int64_t committed = -1;
+    const int u_begin = a.cta_first[blockIdx.x], u_end = a.cta_first[blockIdx.x + 1];
+    const uint32_t limit = a.wait_limit;
 
-    // the CTA's units, in order (one wave of persistent CTAs)
-    const int u_end = a.cta_first[blockIdx.x + 1];
-    for (int ui = a.cta_first[blockIdx.x]; ui < u_end; ++ui) {
-    const WorkUnit wu = a.units[ui];
-    const int tile = wu.tile;
-    const int64_t r0 = int64_t(tile) * TILE_R;
-
-    // unit tables: the 1/(i+1) pairs of every photon number the unit touches
-    // (forward: the unit's photon range; adjoint: the tile's photon range)
-    // and, for the adjoint, the metadata of the unit's probes
-    const int64_t rbase = FWD ? int64_t(wu.k0) : r0;
-    const int64_t rcount = FWD ? int64_t(wu.k1 - wu.k0) + 2 * RUN : int64_t(TILE_R) + 2 * RUN;
-    for (int64_t k = tid; k < rcount; k += TC_THREADS) {
-        const int64_t idx = rbase + k + 1;
-        rinv_s[k] = idx < a.M + RUN + 1 ? a.rinv2[idx] : make_float2(0.f, 0.f);
-    }
-    if (!FWD)
-        for (int64_t k = tid; k < int64_t(wu.k1 - wu.k0); k += TC_THREADS) meta_s[k] = load_meta(a, wu.k0 + k);
-    // forward: every thread generates the runs of one probe (row tid % 128)
-    const ProbeMeta my_meta = FWD ? load_meta(a, r0 + (tid % TILE_R)) : ProbeMeta{1, 0, 0, make_float2(0.f, 0.f)};
-    __syncthreads();
-
-    constexpr uint32_t IDESC = tc::idesc_bf16_f32(TILE_R, BN);
-    const int nsteps = (wu.k1 - wu.k0) / TC_BK;
-
-    // anchors of a slice: loaded one slice ahead so their latency overlaps the
-    // current slice's arithmetic
-    constexpr int QRUNS = (TILE_R * TC_BK / RUN) / TC_THREADS;
-    auto run_probe = [&](int64_t k0, int q, ProbeMeta &m, int64_t &i_r, int &row, int &chunk) {
-        const int run = tid + q * TC_THREADS;
-        if (FWD) {
-            row = run % TILE_R;
-            chunk = run / TILE_R;
-            m = my_meta;
-            i_r = k0 + int64_t(chunk) * RUN;
-        } else {
-            const int g = run >> 3, t = run & 7;
-            const int pb = g % (TILE_R / 8), kb = g / (TILE_R / 8);
-            const int64_t dk = k0 + kb * 8 + t;
-            m = (dk < wu.k1) ? meta_s[dk - wu.k0] : ProbeMeta{1, 0, 0, make_float2(0.f, 0.f)};
-            i_r = r0 + pb * 8;
-            row = pb * 8 + t;
-            chunk = kb;
-        }
-    };
-    float anc_next[QRUNS];
-    if (nsteps > 0) {
-#pragma unroll
-        for (int q = 0; q < QRUNS; ++q) {
-            ProbeMeta m; int64_t i_r; int row, chunk;
-            run_probe(int64_t(wu.k0), q, m, i_r, row, chunk);
-            anc_next[q] = anchor_of(a.anchor, m, i_r);
-        }
-    }
-
-    // operand B of one step: the transposed bf16 copy of the vector, 16-byte
-    // asynchronous copies into B stage `bs`, as one copy group
-    constexpr int BCH = BN * (TC_BK / 8);          // 16-byte chunks per part
-    auto issue_b = [&](int64_t kb0, int bs) {
-        unsigned char *B_hi = sm + TC_STAGES * L::A_STAGE + bs * L::B_STAGE;
-        unsigned char *B_lo = B_hi + L::B_BYTES;
-#pragma unroll
-        for (int q = 0; q < (L::NPART * BCH + TC_THREADS - 1) / TC_THREADS; ++q) {
-            const int c = tid + q * TC_THREADS;
-            if (c < L::NPART * BCH) {
-                const int part = c / BCH, cc = c % BCH;
-                const int n = cc / (TC_BK / 8), j = cc % (TC_BK / 8);
-                const __nv_bfloat16 *src = (part == 0 ? a.b_hi : a.b_lo) + (n0 + n) * a.bpitch + kb0 + j * 8;
-                cp_async16((part == 0 ? B_hi : B_lo) + tc::sw128_chunk(n, j), src);
-            }
-        }
-        cp_async_commit();
-    };
-
-    for (int s = 0; s < nsteps; ++s) {
-        const uint32_t g = gstep + uint32_t(s);
-        const int st = int(g % TC_STAGES);            // A stage and MMA barrier
-        const int bst = int(g % TC_BSTAGES);          // B stage
-        unsigned char *A_hi = sm + st * L::A_STAGE;
-        unsigned char *A_lo = A_hi + L::A_BYTES;                        // SPLIT == 3 only
-        unsigned char *B_hi = sm + TC_STAGES * L::A_STAGE + bst * L::B_STAGE;
-        unsigned char *B_lo = B_hi + L::B_BYTES;                        // SPLIT == 3 only
-        if (g >= TC_STAGES) {
-            // the MMAs of step g - 2 (maybe of the previous unit) read this A
-            // stage and the B stage of step g + 1; their completion also
-            // covers every earlier step
-            if (!tc::mbar_wait_bounded(&bars[st], ((g / TC_STAGES) - 1) & 1u, a.wait_limit))
-                ok = false;
-        }
-        const int64_t k0 = int64_t(wu.k0) + int64_t(s) * TC_BK;
-
-        // ---- operand B: this step's copy (first step of a unit) and the
-        // next step's, so that a copy's latency overlaps a whole step ----
-        if (s == 0) issue_b(k0, bst);
-        if (s + 1 < nsteps) issue_b(k0 + TC_BK, int((g + 1) % TC_BSTAGES));
-        // ---- operand A: Poisson weights ----
-        float anc_cur[QRUNS];
-#pragma unroll
-        for (int q = 0; q < QRUNS; ++q) anc_cur[q] = anc_next[q];
-        if (s + 1 < nsteps) {
-#pragma unroll
-            for (int q = 0; q < QRUNS; ++q) {
-                ProbeMeta m; int64_t i_r; int row, chunk;
-                run_probe(k0 + TC_BK, q, m, i_r, row, chunk);
-                anc_next[q] = anchor_of(a.anchor, m, i_r);
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < QRUNS; ++q) {
-            ProbeMeta m; int64_t i_r; int row, chunk;
-            run_probe(k0, q, m, i_r, row, chunk);
-            float v8[RUN];
-            if (FWD) {
-                // row = probe r0 + r, chunk = photon numbers k0 + 8 j .. + 7
-                tc_expand_run(anc_cur[q], m, i_r, rinv_s, rbase, v8);
-            } else {
-                // 8 x 8 block (8 probes x 8 photon numbers) per group of 8
-                // lanes, transposed through shared memory so that one lane
-                // holds 8 consecutive probes of one photon number
-                const int t = (tid + q * TC_THREADS) & 7;
-                float w8[RUN];
-                tc_expand_run(anc_cur[q], m, i_r, rinv_s, rbase, w8);
-                float *stg = staging + ((tid >> 3) * 8) * 9;
-#pragma unroll
-                for (int j = 0; j < RUN; ++j) stg[t * 9 + j] = w8[j];
-                __syncwarp();
-#pragma unroll
-                for (int j = 0; j < RUN; ++j) v8[j] = stg[j * 9 + t];
-                __syncwarp();
-            }
-            uint4 hi, lo;
-            split_pack(v8, hi, lo);
-            *reinterpret_cast<uint4 *>(A_hi + tc::sw128_chunk(row, chunk)) = hi;
-            if (SPLIT == 3) *reinterpret_cast<uint4 *>(A_lo + tc::sw128_chunk(row, chunk)) = lo;
-        }
-        // this step's B copy is complete when at most the next step's group
-        // is still in flight
-        if (s + 1 < nsteps) cp_async_wait_group1();
-        else cp_async_wait_all();
-        tc::fence_proxy_async_smem();
-        tc::tc_fence_before_sync();
-        // a wait that gave up in any thread stops the CTA here, uniformly and
-        // before any further MMA is issued (the stages it would overwrite may
-        // still be read by MMAs in flight)
-        if (__syncthreads_or(ok ? 0 : 1)) {
-            ok = false;
-            break;
-        }
-        if (!a.skip_mma) committed = int64_t(g);
-        if (tid == 0 && !a.skip_mma) {
-            tc::tc_fence_after_sync();
-            const uint32_t a_hi = tc::smem_u32(A_hi), a_lo = tc::smem_u32(A_lo);
-            const uint32_t b_hi = tc::smem_u32(B_hi), b_lo = tc::smem_u32(B_lo);
-#pragma unroll
-            for (int kk = 0; kk < TC_BK / 16; ++kk) {
-                const uint32_t off = kk * 32;   // 16 bf16 per MMA
-                const uint32_t acc0 = (s > 0 || kk > 0) ? 1u : 0u;
-                tc::mma_bf16(tmem, tc::desc_kmajor_sw128(a_hi + off), tc::desc_kmajor_sw128(b_hi + off), IDESC, acc0);
-                if (SPLIT == 3) {
-                    tc::mma_bf16(tmem, tc::desc_kmajor_sw128(a_hi + off), tc::desc_kmajor_sw128(b_lo + off), IDESC, 1u);
-                    tc::mma_bf16(tmem, tc::desc_kmajor_sw128(a_lo + off), tc::desc_kmajor_sw128(b_hi + off), IDESC, 1u);
+    if (warp < TC_MMA_WARP) {
+        // ------------------------------------------------------------ producers
+        // Per-slice tables live in shared memory, loaded two slices ahead by
+        // the first 64 producer threads: the forward's ratios 1/(i+1) of the
+        // slice's photon numbers, the adjoint's probe metadata of the slice's
+        // probes (its ratios cover the whole tile and are loaded per unit).
+        // Producer-wide agreement (tables written, a wait given up) goes
+        // through one bounded barrier with an OR reduction per slice.
+        constexpr int QRUNS = (TILE_R * TC_BK / RUN) / TC_PROD;       // 4 runs of 8 per thread
+        float *stg = staging + ((tid >> 3) * 8) * 9;
+        float2 (*win_r)[TC_BK] = reinterpret_cast<float2 (*)[TC_BK]>(sm + L::TAB_OFF);
+        ProbeMeta (*win_m)[TC_BK] = reinterpret_cast<ProbeMeta (*)[TC_BK]>(sm + L::TAB_OFF + TC_WIN * TC_BK * 8);
+        float2 *rtile = reinterpret_cast<float2 *>(sm + L::TAB_OFF + TC_WIN * TC_BK * (8 + 24));
+        const ProbeMeta none{1, 0, 0, make_float2(0.f, 0.f)};
+        uint32_t g = 0;
+        bool ok = true;
+        for (int ui = u_begin; ui < u_end && ok; ++ui) {
+            const WorkUnit wu = a.units[ui];
+            const int nsteps = (wu.k1 - wu.k0) / TC_BK;
+            if (nsteps == 0) continue;
+            const int64_t r0 = int64_t(wu.tile) * TILE_R;
+            // forward: every thread expands runs of one probe (row tid % 128)
+            const ProbeMeta my = FWD ? load_meta(a, r0 + (tid % TILE_R)) : none;
+            // entry tid (< 64) of the table of slice j
+            auto load_tab = [&](int j, float2 &rv, ProbeMeta &mv) {
+                const int64_t k0j = int64_t(wu.k0) + int64_t(j) * TC_BK;
+                if (FWD) {
+                    const int64_t idx = k0j + tid + 1;
+                    rv = idx <= a.M + RUN ? __ldg(&a.rinv2[idx]) : make_float2(0.f, 0.f);
+                } else {
+                    const int64_t d = k0j + tid;
+                    mv = d < wu.k1 ? load_meta(a, d) : none;
                 }
+            };
+            auto store_tab = [&](int j, const float2 &rv, const ProbeMeta &mv) {
+                if (FWD) win_r[j % TC_WIN][tid] = rv;
+                else win_m[j % TC_WIN][tid] = mv;
+            };
+            // the anchors of every run of slice j (tables of slice j in place)
+            float anc[QRUNS];
+            auto fetch_anchors = [&](int j) {
+                const int64_t k0j = int64_t(wu.k0) + int64_t(j) * TC_BK;
+#pragma unroll
+                for (int q = 0; q < QRUNS; ++q) {
+                    const int run = tid + q * TC_PROD;
+                    if (FWD) {
+                        anc[q] = anchor_of(a.anchor, my, k0j + int64_t(run / TILE_R) * RUN);
+                    } else {
+                        const int g8 = run >> 3, t = run & 7;
+                        const int pb = g8 % (TILE_R / 8), kb = g8 / (TILE_R / 8);
+                        anc[q] = anchor_of(a.anchor, win_m[j % TC_WIN][kb * 8 + t], r0 + pb * 8);
+                    }
+                }
+            };
+            {   // prologue of the unit: tables of slices 0 and 1, the adjoint's ratios
+                // (after every producer is done with the previous unit's tables)
+                producers_sync_or(false);
+                float2 rv = make_float2(0.f, 0.f);
+                ProbeMeta mv = none;
+                if (tid < TC_BK) {
+                    load_tab(0, rv, mv);
+                    store_tab(0, rv, mv);
+                    if (nsteps > 1) {
+                        load_tab(1, rv, mv);
+                        store_tab(1, rv, mv);
+                    }
+                }
+                if (!FWD)
+                    for (int k = tid; k < TILE_R + RUN; k += TC_PROD) {
+                        const int64_t idx = r0 + k + 1;
+                        rtile[k] = idx <= a.M + RUN ? __ldg(&a.rinv2[idx]) : make_float2(0.f, 0.f);
+                    }
+                producers_sync_or(false);
+                fetch_anchors(0);
             }
-            tc::mma_commit(&bars[st]);
+            for (int s = 0; s < nsteps; ++s, ++g) {
+                const int st = int(g % TC_SA);
+                bool wok = true;
+                if (g >= TC_SA) wok = warp_wait(&a_empty[st], ((g / TC_SA) - 1) & 1u, limit, abort_flag);
+                // every producer is past slice s - 1: the tables of slice s + 1
+                // are written and the window of slice s - 1 may be reused
+                if (producers_sync_or(!wok)) {
+                    *abort_flag = 1;
+                    ok = false;
+                    break;
+                }
+                float2 rv = make_float2(0.f, 0.f);
+                ProbeMeta mv = none;
+                if (tid < TC_BK && s + 2 < nsteps) load_tab(s + 2, rv, mv);
+                unsigned char *A_hi = sm + st * L::A_STAGE;
+                unsigned char *A_lo = A_hi + L::A_BYTES;
+                const int64_t k0 = int64_t(wu.k0) + int64_t(s) * TC_BK;
+                const int w = s % TC_WIN;
+                float ac[QRUNS];
+#pragma unroll
+                for (int q = 0; q < QRUNS; ++q) ac[q] = anc[q];
+                if (s + 1 < nsteps) fetch_anchors(s + 1);
+#pragma unroll
+                for (int q = 0; q < QRUNS; ++q) {
+                    const int run = tid + q * TC_PROD;
+                    float v8[RUN];
+                    int row, chunk;
+                    if (FWD) {
+                        // row = probe r0 + row, chunk = photon numbers k0 + 8 chunk .. + 7
+                        row = run % TILE_R;
+                        chunk = run / TILE_R;
+                        tc_expand_run(ac[q], my.lam, my.lo, my.hi, int32_t(k0) + chunk * RUN, &win_r[w][chunk * RUN], v8);
+                    } else {
+                        // 8 x 8 block (8 probes x 8 photon numbers) per group of 8
+                        // lanes, transposed through shared memory so that one lane
+                        // holds 8 consecutive probes of one photon number
+                        const int g8 = run >> 3, t = run & 7;
+                        const int pb = g8 % (TILE_R / 8), kb = g8 / (TILE_R / 8);
+                        row = pb * 8 + t;
+                        chunk = kb;
+                        float w8[RUN];
+                        const ProbeMeta &m = win_m[w][kb * 8 + t];
+                        tc_expand_run(ac[q], m.lam, m.lo, m.hi, int32_t(r0) + pb * 8, &rtile[pb * 8], w8);
+#pragma unroll
+                        for (int j = 0; j < RUN; ++j) stg[t * 9 + j] = w8[j];
+                        __syncwarp();
+#pragma unroll
+                        for (int j = 0; j < RUN; ++j) v8[j] = stg[j * 9 + t];
+                        __syncwarp();
+                    }
+                    uint4 hi, lo;
+                    split_pack(v8, hi, lo);
+                    *reinterpret_cast<uint4 *>(A_hi + tc::sw128_chunk(row, chunk)) = hi;
+                    *reinterpret_cast<uint4 *>(A_lo + tc::sw128_chunk(row, chunk)) = lo;
+                }
+                if (tid < TC_BK && s + 2 < nsteps) store_tab(s + 2, rv, mv);
+                // the generic-proxy stores become visible to the tensor core
+                tc::fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&a_full[st]);
+            }
+        }
+    } else if (warp == TC_MMA_WARP) {
+        // ------------------------------------------- TMA of B, MMA issue (lane 0)
+        if (lane == 0) {
+            constexpr uint32_t IDESC = tc::idesc_bf16_f32(TILE_R, BN);
+            // cursor over the CTA's slices in order, skipping empty units
+            struct Cur { int ui, s, ns; int64_t k0; };
+            auto seek = [&](Cur &c) {
+                while (c.ui < u_end) {
+                    const WorkUnit w = a.units[c.ui];
+                    c.ns = (w.k1 - w.k0) / TC_BK;
+                    c.k0 = w.k0;
+                    if (c.s < c.ns) return;
+                    ++c.ui;
+                    c.s = 0;
+                }
+            };
+            Cur tc_cur{u_begin, 0, 0, 0};
+            seek(tc_cur);
+            uint32_t issued = 0, consumed = 0;
+            int64_t last_commit = -1;
+            auto issue_b = [&](Cur &c) {
+                const int bs = int(issued % TC_SB);
+                unsigned char *B_hi = sm + L::B_OFF + bs * L::B_STAGE;
+                const int32_t x = int32_t(c.k0 + int64_t(c.s) * TC_BK);
+                tc::mbar_arrive_expect_tx(&b_full[bs], 2u * L::B_BYTES);
+                tc::tma_load_2d(B_hi, &a.tm_b_hi, x, int32_t(n0), &b_full[bs]);
+                tc::tma_load_2d(B_hi + L::B_BYTES, &a.tm_b_lo, x, int32_t(n0), &b_full[bs]);
+                ++issued;
+                ++c.s;
+                seek(c);
+            };
+            for (int j = 0; j < 2 && tc_cur.ui < u_end; ++j) issue_b(tc_cur);
+            uint32_t g = 0, au = 0;
+            bool ok = true;
+            for (int ui = u_begin; ui < u_end && ok; ++ui) {
+                const WorkUnit wu = a.units[ui];
+                const int nsteps = (wu.k1 - wu.k0) / TC_BK;
+                if (nsteps == 0) continue;
+                const int acc = int(au & 1u);
+                if (au >= 2 && !tc::mbar_wait_or_abort(&acc_empty[acc], ((au >> 1) - 1) & 1u, limit, abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                tc::tc_fence_after_sync();
+                const uint32_t d_tmem = tmem + uint32_t(acc * L::ACC_COLS);
+                for (int s = 0; s < nsteps; ++s, ++g) {
+                    const int st = int(g % TC_SA), bs = int(g % TC_SB);
+                    if (!tc::mbar_wait_or_abort(&b_full[bs], (g / TC_SB) & 1u, limit, abort_flag)) { ok = false; break; }
+                    ++consumed;
+                    if (!tc::mbar_wait_or_abort(&a_full[st], (g / TC_SA) & 1u, limit, abort_flag)) { ok = false; break; }
+                    tc::tc_fence_after_sync();
+                    if (!a.skip_mma) {
+                        const uint32_t a_hi = tc::smem_u32(sm + st * L::A_STAGE), a_lo = a_hi + L::A_BYTES;
+                        const uint32_t b_hi = tc::smem_u32(sm + L::B_OFF + bs * L::B_STAGE), b_lo = b_hi + L::B_BYTES;
+#pragma unroll
+                        for (int kk = 0; kk < TC_BK / 16; ++kk) {
+                            const uint32_t off = kk * 32;   // 16 bf16 per MMA
+                            const uint32_t acc0 = (s > 0 || kk > 0) ? 1u : 0u;
+                            tc::mma_bf16(d_tmem, tc::desc_kmajor_sw128(a_hi + off), tc::desc_kmajor_sw128(b_hi + off), IDESC, acc0);
+                            tc::mma_bf16(d_tmem, tc::desc_kmajor_sw128(a_hi + off), tc::desc_kmajor_sw128(b_lo + off), IDESC, 1u);
+                            tc::mma_bf16(d_tmem, tc::desc_kmajor_sw128(a_lo + off), tc::desc_kmajor_sw128(b_hi + off), IDESC, 1u);
+                        }
+                        tc::mma_commit(&a_empty[st]);
+                        last_commit = int64_t(g);
+                    }
+                    // the B copy of slice `issued` (= g + 2) reuses the stage of
+                    // slice g - 1: its MMAs must be complete
+                    if (tc_cur.ui < u_end) {
+                        if (g >= 1 && !tc::mbar_wait_or_abort(&a_empty[(g - 1) % TC_SA], ((g - 1) / TC_SA) & 1u,
+                                                              limit, abort_flag)) {
+                            ok = false;
+                            break;
+                        }
+                        issue_b(tc_cur);
+                    }
+                }
+                if (!ok) break;
+                if (!a.skip_mma) tc::mma_commit(&acc_full[acc]);
+                ++au;
+            }
+            if (!ok) {
+                *abort_flag = 1;
+                // nothing may still target this CTA's memory when it exits:
+                // the B copies issued but not consumed, and the last group of
+                // committed MMAs (its completion covers all earlier ones)
+                for (uint32_t j = consumed; j < issued; ++j)
+                    tc::mbar_wait_bounded(&b_full[j % TC_SB], (j / TC_SB) & 1u, limit);
+                if (last_commit >= 0)
+                    tc::mbar_wait_bounded(&a_empty[uint32_t(last_commit) % TC_SA],
+                                          (uint32_t(last_commit) / TC_SA) & 1u, limit);
+            }
+        }
+    } else {
+        // ---------------------------------------------------------- epilogue
+        const int q = warp & 3;                 // tensor-memory lanes 32 q .. 32 q + 31
+        const int ncb = gridDim.y;
+        constexpr int TE = TILE_R * BN;
+        uint32_t au = 0;
+        for (int ui = u_begin; ui < u_end; ++ui) {
+            const WorkUnit wu = a.units[ui];
+            const int nsteps = (wu.k1 - wu.k0) / TC_BK;
+            // partial tile of the unit, column-major: column c at c * 128
+            float *dst = a.part + (int64_t(a.tile_first[wu.tile] + wu.chunk) * ncb + blockIdx.y) * TE + 32 * q + lane;
+            if (nsteps == 0) {
+#pragma unroll 8
+                for (int c = 0; c < BN; ++c) dst[c * TILE_R] = 0.f;
+                continue;
+            }
+            const int acc = int(au & 1u);
+            if (!warp_wait(&acc_full[acc], (au >> 1) & 1u, limit, abort_flag)) {
+                *abort_flag = 1;
+                break;
+            }
+            tc::tc_fence_after_sync();
+#pragma unroll
+            for (int c0 = 0; c0 < BN; c0 += 32) {
+                uint32_t r[32];
+                tc::tmem_ld_32x32b_x32(tmem + (uint32_t(32 * q) << 16) + uint32_t(acc * L::ACC_COLS + c0), r);
+#pragma unroll
+                for (int k = 0; k < 32; ++k) dst[(c0 + k) * TILE_R] = __uint_as_float(r[k]);
+            }
+            tc::tc_fence_before_sync();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&acc_empty[acc]);
+            ++au;
         }
     }
-    if (ok && nsteps > 0) {
-        const uint32_t g = gstep + uint32_t(nsteps - 1);
-        if (!tc::mbar_wait_bounded(&bars[g % TC_STAGES], (g / TC_STAGES) & 1u, a.wait_limit))
-            ok = false;
-    }
-    gstep += uint32_t(nsteps);
-    tc::tc_fence_after_sync();
-    if (__syncthreads_or(ok ? 0 : 1)) {
-        ok = false;
-        break;
-    }
-
-    // ---- this unit's f32 partial tile (split-K) ----
-    // through a shared-memory copy (the stage buffers: every MMA and copy of
-    // this unit is complete) so that the global writes run along rows.  The
-    // finish kernel sums the partials of every tile in unit order and runs
-    // the epilogue, spread over many CTAs.  Warp w reads TMEM lanes
-    // 32 (w % 4) .. + 31 (tile rows) and the column half w / 4 (BN >= 64) or
-    // all columns (BN == 32, warps 0-3 only).
-    const int lg = warp & 3;
-    const int row = lg * 32 + lane;
-    constexpr int COLS_PER_WARP = BN >= 64 ? BN / 2 : BN;
-    const int col0 = BN >= 64 ? (warp >> 2) * COLS_PER_WARP : 0;
-    const bool active = BN >= 64 || warp < 4;
-    const int ncb = gridDim.y;
-    constexpr int LD = BN + 1;                 // padded row: conflict-free both ways
-    constexpr int TE = TILE_R * BN;
-    float *tile_s = reinterpret_cast<float *>(sm);
-    if (active) {
-#pragma unroll
-        for (int c = 0; c < COLS_PER_WARP; c += 32) {
-            uint32_t r[32];
-            if (nsteps > 0) {
-                tc::tmem_ld_32x32b_x32(tmem + (uint32_t(lg * 32) << 16) + uint32_t(col0 + c), r);
-            } else {
-#pragma unroll
-                for (int k = 0; k < 32; ++k) r[k] = 0u;
-            }
-#pragma unroll
-            for (int k = 0; k < 32; ++k) tile_s[row * LD + col0 + c + k] = __uint_as_float(r[k]);
-        }
-    }
-    __syncthreads();
-    {
-        float *mine = a.part + (int64_t(a.tile_first[tile] + wu.chunk) * ncb + blockIdx.y) * TE;
-        for (int e = tid; e < TE; e += TC_THREADS) mine[e] = tile_s[(e / BN) * LD + (e % BN)];
-    }
-    // the next unit's first MMA overwrites the accumulator and its tables
-    // replace these: every thread is past its tensor-memory loads
     tc::tc_fence_before_sync();
     __syncthreads();
-    }  // units
-    if (!ok) {
-        // the CTA gave up: no copy may still target its shared memory and no
-        // committed MMA may still write its tensor memory when it is freed,
-        // so wait for the copies and, once more with a bound, for the last
-        // committed group of MMAs (their completion covers all earlier ones)
-        cp_async_wait_all();
-        if (committed >= 0) {
-            const uint32_t g = uint32_t(committed);
-            tc::mbar_wait_bounded(&bars[g % TC_STAGES], (g / TC_STAGES) & 1u, a.wait_limit);
-        }
-        tc::tc_fence_after_sync();
-        __syncthreads();
-    }
+    tc::tc_fence_after_sync();
     if (warp == 0) tc::tmem_dealloc(tmem, L::TMEM_COLS);
-    if (!ok && tid == 0) atomicExch(a.err, 1);
+    if (*abort_flag && tid == 0) atomicExch(a.err, 1);
 }
 
 
@@ -526,21 +570,24 @@ __global__ void __launch_bounds__(FIN_T) k_tc_finish(TcArgs a)
     const int ncb = gridDim.y;
     const int nsplit = a.tile_nsplit[tile];
     const int64_t split_stride = int64_t(ncb) * TE;
+    // partial tiles are column-major (column c at c * 128): float4 f of the
+    // slice holds rows rq * 32 + 4 (f % 8) .. + 3 of column f / 8
     const float4 *base = reinterpret_cast<const float4 *>(
-        a.part + (int64_t(a.tile_first[tile]) * ncb + blockIdx.y) * TE + int64_t(rq) * IE);
+        a.part + (int64_t(a.tile_first[tile]) * ncb + blockIdx.y) * TE) + rq * (FIN_RB / 4);
+    auto f4_at = [](int f) { return (f >> 3) * (TILE_R / 4) + (f & 7); };
 
     float4 acc[P4], cur[P4];
 #pragma unroll
     for (int j = 0; j < P4; ++j) {
         acc[j] = make_float4(0.f, 0.f, 0.f, 0.f);
-        cur[j] = __ldcg(base + tid + j * FIN_T);
+        cur[j] = __ldcg(base + f4_at(tid + j * FIN_T));
     }
     for (int sidx = 0; sidx < nsplit; ++sidx) {
         float4 nxt[P4];
         if (sidx + 1 < nsplit) {
             const float4 *src = base + (sidx + 1) * (split_stride / 4);
 #pragma unroll
-            for (int j = 0; j < P4; ++j) nxt[j] = __ldcg(src + tid + j * FIN_T);
+            for (int j = 0; j < P4; ++j) nxt[j] = __ldcg(src + f4_at(tid + j * FIN_T));
         }
 #pragma unroll
         for (int j = 0; j < P4; ++j) {
@@ -553,9 +600,11 @@ __global__ void __launch_bounds__(FIN_T) k_tc_finish(TcArgs a)
     }
 #pragma unroll
     for (int j = 0; j < P4; ++j) {
-        const int e = (tid + j * FIN_T) * 4, rr = e / BN, cc = e % BN;
-        float *d = &zs[rr * LD + cc];
-        d[0] = acc[j].x; d[1] = acc[j].y; d[2] = acc[j].z; d[3] = acc[j].w;
+        const int f = tid + j * FIN_T, cc = f >> 3, rr = 4 * (f & 7);
+        zs[rr * LD + cc] = acc[j].x;
+        zs[(rr + 1) * LD + cc] = acc[j].y;
+        zs[(rr + 2) * LD + cc] = acc[j].z;
+        zs[(rr + 3) * LD + cc] = acc[j].w;
     }
     __syncthreads();
 
@@ -807,11 +856,11 @@ k_cg_update_p_split(const int32_t *gate, const double *beta_p, int64_t M, int64_
 // ----------------------------------------------------------------------------
 // launchers
 // ----------------------------------------------------------------------------
-template <int BN, int SPLIT, bool FWD>
+template <int BN, bool FWD>
 static cudaError_t launch_tc_t(Plan &p, const TcArgs &a)
 {
-    auto kern = k_band_tc<BN, SPLIT, FWD>;
-    const int smem = TcLayout<BN, SPLIT>::TOTAL;
+    auto kern = k_band_tc<BN, FWD>;
+    const int smem = TcLayout<BN>::TOTAL;
     static const cudaError_t cfg =
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (cfg != cudaSuccess) return cfg;
@@ -832,22 +881,24 @@ template <bool FWD>
 static cudaError_t launch_tc(Plan &p, const TcArgs &a)
 {
     switch (band_bn(p.N)) {
-    case 128: return launch_tc_t<128, 3, FWD>(p, a);
-    case 64: return launch_tc_t<64, 3, FWD>(p, a);
-    default: return launch_tc_t<32, 3, FWD>(p, a);
+    case 128: return launch_tc_t<128, FWD>(p, a);
+    case 64: return launch_tc_t<64, FWD>(p, a);
+    default: return launch_tc_t<32, FWD>(p, a);
     }
 }
 
 static TcArgs tc_args(Plan &p, bool fwd, const int32_t *gate)
 {
     TcArgs a;
+    a.tm_b_hi = fwd ? p.tm_ut_hi : p.tm_ot_hi;
+    a.tm_b_lo = fwd ? p.tm_ut_lo : p.tm_ot_lo;
     a.M = p.M; a.N = p.N; a.D = p.D;
     a.lam2 = p.lam_f2; a.lo = p.lo; a.hi = p.hi; a.aoff = p.aoff;
     a.anchor = p.anchor_f; a.rinv2 = p.ratio_inv_f2;
     const Schedule &S = p.sched_tc[fwd ? 0 : 1];
     a.units = S.units; a.cta_first = S.cta_first;
     a.tile_first = S.tile_first; a.tile_nsplit = S.tile_nsplit;
-    a.counters = S.counters; a.part = reinterpret_cast<float *>(S.part);
+    a.part = reinterpret_cast<float *>(S.part);
     a.gate = gate;
     a.err = &p.sc->tc_err;
     a.b_hi = fwd ? p.ut_hi : p.ot_hi;
@@ -920,10 +971,10 @@ cudaError_t launch_hvp_tc(Plan &p, const void *V, void *HV, bool vec_f32, bool g
 }
 
 // Self-test of the bounded waits: one Hessian product (double vectors) whose
-// MMAs are withheld, so no mbarrier ever completes; with waits bounded at 4096
-// polls every CTA gives up after its first unit, sets the error flag and
-// returns.  Nothing is left in flight (no MMA was issued, every copy is waited
-// for), so the context stays usable; the host re-arms the counters.
+// MMAs are withheld, so the stage and accumulator barriers never complete;
+// with waits bounded at 4096 polls every CTA gives up, raises its abort flag,
+// sets the error flag and returns.  Nothing is left in flight (no MMA was
+// issued, every TMA copy is waited for), so the context stays usable.
 cudaError_t launch_hvp_tc_wait_selftest(Plan &p, const double *V, double *HV)
 {
     dim3 tb(32, 8), tg(unsigned((p.M + 31) / 32), unsigned((p.N + 31) / 32));
@@ -945,9 +996,33 @@ cudaError_t launch_hvp_tc_wait_selftest(Plan &p, const double *V, double *HV)
 
 size_t tc_smem_bytes(int bn)
 {
-    if (bn == 128) return TcLayout<128, 3>::TOTAL;
-    if (bn == 64) return TcLayout<64, 3>::TOTAL;
-    return TcLayout<32, 3>::TOTAL;
+    if (bn == 128) return TcLayout<128>::TOTAL;
+    if (bn == 64) return TcLayout<64>::TOTAL;
+    return TcLayout<32>::TOTAL;
+}
+
+// Tensor map of a transposed bf16 operand copy (rows x pitch elements, pitch
+// a multiple of 64): boxes of 64 elements x bn rows with the 128-byte swizzle
+// of the MMA operand layout.  The driver's encoder is looked up once.
+cudaError_t encode_operand_map(CUtensorMap *map, const void *base, int64_t pitch, int64_t rows, int bn)
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess) return e;
+        if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    const cuuint64_t dims[2] = {cuuint64_t(pitch), cuuint64_t(rows)};
+    const cuuint64_t strides[1] = {cuuint64_t(pitch) * sizeof(__nv_bfloat16)};
+    const cuuint32_t box[2] = {cuuint32_t(TC_BK), cuuint32_t(bn)};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box,
+                              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 }  // namespace tomo

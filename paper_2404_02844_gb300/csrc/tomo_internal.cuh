@@ -2,6 +2,7 @@
 // units of libtomo (plan kernels, band contractions, row kernels, host API).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -23,7 +24,7 @@ namespace tomo {
 constexpr int RUN = 8;
 constexpr int TILE_R = 128;
 constexpr int GEMM_THREADS = 256;
-constexpr int TC_MAX_UNIT = 1024;         // longest reduction range of a tensor-core work unit
+constexpr int TC_MAX_UNIT = 4096;         // longest reduction range of a tensor-core work unit (split schedules)
 constexpr int ROW_WARPS = 8;              // warps per CTA in row kernels
 constexpr int MAX_N = 1024;               // outcomes supported by row kernels
 constexpr int RED_SLOTS = 4;              // partial-sum slots per reduction
@@ -100,9 +101,11 @@ struct Plan {
     int fwd_tiles, adj_tiles;
     Schedule sched[2][2];      // [forward, adjoint][float, double]
     Schedule sched_tc[2];      // tensor-core contractions [forward, adjoint]
-    // transposed bf16 hi/lo copies of the tensor-core operands
+    // transposed bf16 hi/lo copies of the tensor-core operands and their
+    // tensor maps (TMA boxes of 64 x BN, 128-byte swizzle)
     __nv_bfloat16 *ut_hi, *ut_lo, *ot_hi, *ot_lo;
     int64_t ut_pitch, ot_pitch;
+    CUtensorMap tm_ut_hi, tm_ut_lo, tm_ot_hi, tm_ot_lo;
 
     // solver execution: a plan-owned non-blocking work stream fenced against
     // the caller's stream, and CUDA graphs of the CG chunk per (stage, profile)
@@ -199,6 +202,11 @@ bool tc_update_p_fusable(const Plan &p);
 cudaError_t launch_cg_update_p_split(Plan &p, int stage);
 cudaError_t launch_hvp_tc_wait_selftest(Plan &p, const double *V, double *HV);
 size_t tc_smem_bytes(int bn);
+// tensor map of a transposed bf16 operand copy (rows x pitch, box 64 x bn)
+cudaError_t encode_operand_map(CUtensorMap *map, const void *base, int64_t pitch, int64_t rows, int bn);
+
+// warmstart.cu: shape of a warm-start handle (false for NULL)
+bool ws_shape(const void *handle, int64_t *D, int64_t *M, int64_t *C0);
 
 // records a failure message for tomo_last_error (api.cu)
 tomo_status tomo_set_error(tomo_status s, const char *msg);

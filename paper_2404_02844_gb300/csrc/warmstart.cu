@@ -355,6 +355,18 @@ struct WarmStart {
     int32_t *ncols;
 };
 
+// Shape of a warm-start handle (probes, photon numbers, padded outcome
+// columns) for the callers that pair it with a plan; false for NULL.
+bool ws_shape(const void *handle, int64_t *D, int64_t *M, int64_t *C0)
+{
+    const WarmStart *w = static_cast<const WarmStart *>(handle);
+    if (!w) return false;
+    *D = w->s.D;
+    *M = w->s.M;
+    *C0 = w->s.C0;
+    return true;
+}
+
 }  // namespace tomo
 
 // ------------------------------------------------------------------ host side

@@ -20,7 +20,9 @@ if ROOT not in sys.path:
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--config", default="c2", choices=["c1", "c2"])
+    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3s"],
+                    help="c3s: the megascale geometry at 1/8 size (M = D = 131072, N = 100, "
+                         "lambda linear in [0, 0.9 M], band +-10 sqrt(lambda); products only)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "mixed", "tc"])
     ap.add_argument("--newton", type=int, default=3)
     ap.add_argument("--op", default="fit", choices=["fit", "hvp", "fwd", "adj"],
@@ -38,6 +40,21 @@ def main():
     from paper_2404_02844_gb300 import build
 
     build.build()
+    if args.config == "c3s":
+        M = D = 131072
+        N = 100
+        lam = workloads.probe_intensities(D, 0.9 * M)
+        with tomo.Plan(M, N, lam, 10.0, 1e-3, precision=args.precision) as pl:
+            g = torch.Generator(device="cuda").manual_seed(1)
+            X = torch.rand(M, N, dtype=torch.float64, device="cuda", generator=g)
+            pl.hvp(X)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(args.reps):
+                pl.hvp(X)
+            torch.cuda.synchronize()
+            print(f"c3s {args.precision}: {args.reps} x hvp, {(time.perf_counter() - t0) / args.reps * 1e3:.3f} ms each")
+        return
     w = {"c1": workloads.config_c1, "c2": workloads.config_c2}[args.config]()
     P = torch.from_numpy(w.P).cuda()
     with tomo.Plan.from_workload(w, precision=args.precision) as pl:
