@@ -34,6 +34,10 @@ def main():
     ap.add_argument("--concurrency", type=int, default=8)
     ap.add_argument("--eps-kkt", type=float, default=1e-6)
     ap.add_argument("--max-newton", type=int, default=200)
+    ap.add_argument("--serial-sample", type=int, default=0,
+                    help="> 0: time one-at-a-time solves on the first K problems only "
+                         "(the full serial pass is skipped)")
+    ap.add_argument("--no-autotune", action="store_true")
     args = ap.parse_args()
 
     import torch
@@ -69,14 +73,39 @@ def main():
                        f"M ~ U{{256..{args.max_m}}}, N ~ U{{8..128}}, D = 2M",
            "solves": len(problems), "precision": args.precision, "data_s": t_data}
     fs = {}
-    for conc, tune in ((1, False), (args.concurrency, False), (args.concurrency, True)):
+    modes = [] if args.serial_sample > 0 else [(1, False)]
+    modes.append((args.concurrency, False))
+    if not args.no_autotune:
+        modes.append((args.concurrency, True))
+    for conc, tune in modes:
         dt, st, reps = run(conc, tune)
         key = f"conc{conc}_{'tuned' if tune else 'default'}"
         fs[key] = np.array([r["f"] for r in reps])
         out[key] = {"seconds": dt, "solves_per_s": len(problems) / dt,
                     "newton_iters": int(sum(r["iters_s1"] + r["iters_s2"] for r in reps)),
+                    "cg_products": int(sum(r["cg_total"] for r in reps)),
                     "statuses": sorted(set(int(s) for s in st))}
-    ref = fs["conc1_default"]
+        print(json.dumps({key: out[key]}), flush=True)
+    ref = fs[f"conc{args.concurrency}_default"]
+    if args.serial_sample > 0:
+        # one-at-a-time solves of the first K problems against the pool's
+        # results for the same problems
+        k = min(args.serial_sample, len(problems))
+        Ths = [torch.empty(problems[j][0].M, problems[j][0].N, dtype=torch.float64, device="cuda")
+               for j in range(k)]
+        probs = [(problems[j][0].M, problems[j][0].N, problems[j][0].lam, problems[j][0].band_k,
+                  problems[j][1], Ps[j], Ths[j]) for j in range(k)]
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        st, reps = tomo.fit_batched(probs, precision=args.precision, concurrency=1,
+                                    eps_kkt=args.eps_kkt, max_newton=args.max_newton)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t
+        fk = np.array([r["f"] for r in reps])
+        out["serial_sample"] = {"problems": k, "seconds": dt, "solves_per_s": k / dt,
+                                "max_rel_objective_diff_vs_pool": float(np.max(np.abs(fk - ref[:k]) / ref[:k]))}
+    else:
+        ref = fs["conc1_default"]
     out["max_rel_objective_diff"] = float(max(np.max(np.abs(v - ref) / ref) for v in fs.values()))
     print(json.dumps(out), flush=True)
 

@@ -35,6 +35,9 @@ def main():
     ap.add_argument("--eps-kkt", type=float, default=1e-9)
     ap.add_argument("--max-newton", type=int, default=600)
     ap.add_argument("--outcomes", type=int, default=50, help="report the first this many outcomes")
+    ap.add_argument("--max-seconds", type=float, default=0.0,
+                    help="> 0: wall-clock bound of every fit (the variant reports where it stopped)")
+    ap.add_argument("--variants", default="a,b,c")
     args = ap.parse_args()
 
     import torch
@@ -54,19 +57,23 @@ def main():
     K = args.outcomes
     # outcomes the probes cover: some probe sees them with frequency >= 5 %
     covered = np.nonzero(w.P.max(0) >= 0.05)[0]
+    lim = dict(max_seconds=args.max_seconds) if args.max_seconds > 0 else {}
+    want = set(args.variants.split(","))
     for name, gamma, smooth in (("a_no_regularisation", 0.0, False), ("b_gamma_1e-5", 1e-5, False),
                                 ("c_gamma_1e-5_long_range", 1e-5, True)):
+        if name[0] not in want:
+            continue
         with tomo.Plan(w.M, w.N, w.lam, w.band_k, gamma, precision=args.precision) as pl:
             torch.cuda.synchronize()
             t = time.perf_counter()
             if smooth:
                 Th, r1, r2 = pl.fit_smoothed(P, exclude=100, div=50.0, eps_kkt=args.eps_kkt,
-                                             max_newton=args.max_newton)
+                                             max_newton=args.max_newton, **lim)
                 iters = [r1["iters_s1"] + r1["iters_s2"], r2["iters_s2"]]
                 stop = [r1["stop_name"], r2["stop_name"]]
                 kkt = r2["kkt"]
             else:
-                Th, r = pl.fit(P, eps_kkt=args.eps_kkt, max_newton=args.max_newton)
+                Th, r = pl.fit(P, eps_kkt=args.eps_kkt, max_newton=args.max_newton, **lim)
                 iters, stop, kkt = [r["iters_s1"] + r["iters_s2"]], [r["stop_name"]], r["kkt"]
             torch.cuda.synchronize()
             dt = time.perf_counter() - t
@@ -76,10 +83,13 @@ def main():
         cov = covered[covered < K]
         out["variants"][name] = {
             "seconds": dt, "newton_iters": iters, "stop": stop, "kkt": kkt, "f": f,
+            "cg_products": (r1["cg_total"] + r2["cg_total"]) if smooth else r["cg_total"],
             "covered_outcomes": int(len(cov)),
             "mean_fidelity_covered": float(np.nanmean(fid[cov])),
             "min_fidelity_covered": float(np.nanmin(fid[cov])),
             "infidelity": [float(x) for x in inf]}
+        print(json.dumps({name: {k: v for k, v in out["variants"][name].items() if k != "infidelity"}}),
+              flush=True)
     print(json.dumps(out), flush=True)
 
 

@@ -42,6 +42,8 @@ def main():
     ap.add_argument("--labels", default="solver", choices=["solver", "true"])
     ap.add_argument("--label-precision", default="tc", choices=["fp32", "tc", "fp64", "mixed"])
     ap.add_argument("--concurrency", type=int, default=8)
+    ap.add_argument("--fit-seconds", type=float, default=60.0, help="wall-clock bound of every evaluation fit")
+    ap.add_argument("--label-newton", type=int, default=1000, help="Newton cap of the label solves")
     ap.add_argument("--save", default=None)
     args = ap.parse_args()
 
@@ -71,13 +73,15 @@ def main():
             problems.append((w.M, w.N, w.lam, w.band_k, w.gamma, P, Th))
             outs.append(Th)
         sts, reps = tomo.fit_batched(problems, precision=args.label_precision,
-                                     concurrency=args.concurrency, eps_kkt=1e-8, max_newton=3000)
+                                     concurrency=args.concurrency, eps_kkt=1e-8,
+                                     max_newton=args.label_newton, max_seconds=args.fit_seconds)
         torch.cuda.synchronize()
         for b, w in enumerate(wtr):
             Ttr_d[b].zero_()
             Ttr_d[b, :, :w.N] = outs[b]
         t_lab = time.perf_counter() - t0
         kk = np.array([r["kkt"] for r in reps])
+        print(json.dumps({"labels_done_s": t_lab}), flush=True)
         label_info.update({"label_s": t_lab, "label_precision": args.label_precision,
                            "label_solves_per_s": len(wtr) / t_lab,
                            "label_status_ok": int(sum(st in (0, 4) for st in sts)),
@@ -108,15 +112,17 @@ def main():
     for w in wte:
         with tomo.Plan.from_workload(w, precision=args.precision) as pl:
             P = torch.from_numpy(w.P).cuda()
-            _, rref = pl.fit(P, eps_kkt=1e-11, max_newton=5000)   # f_ref (also warms the graphs)
+            _, rref = pl.fit(P, eps_kkt=1e-10, max_newton=3000,
+                             max_seconds=args.fit_seconds)   # f_ref (also warms the graphs)
             target = rref["f"] * (1.0 + 1e-8)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            Thc, rc = pl.fit(P, f_target=target, eps_kkt=0.0, max_newton=5000)
+            Thc, rc = pl.fit(P, f_target=target, eps_kkt=0.0, max_newton=3000, max_seconds=args.fit_seconds)
             torch.cuda.synchronize()
             tc = time.perf_counter() - t0
             t0 = time.perf_counter()
-            Thw, rw, used = tomo.fit_warm(pl, ws, P, f_target=target, eps_kkt=0.0, max_newton=5000)
+            Thw, rw, used = tomo.fit_warm(pl, ws, P, f_target=target, eps_kkt=0.0, max_newton=3000,
+                                          max_seconds=args.fit_seconds)
             torch.cuda.synchronize()
             tw = time.perf_counter() - t0
             fc, fw = pl.objective(P, Thc), pl.objective(P, Thw)
@@ -127,6 +133,7 @@ def main():
                          cold_stop=rc["stop_name"], warm_stop=rw["stop_name"],
                          used_warm=bool(used), rel_gap_cold=(fc - rref["f"]) / rref["f"],
                          rel_gap_warm=(fw - rref["f"]) / rref["f"], f0_warm_over_uniform=f0w / f0u))
+        print(json.dumps({"test": len(rows), **rows[-1]}), flush=True)
     ci = np.array([r["cold_iters"] for r in rows])
     wi = np.array([r["warm_iters"] for r in rows])
     out = {

@@ -151,3 +151,50 @@ def test_training_lowers_the_loss_and_warm_starts_save_iterations(tomo):
             cold.append(rc["iters_s1"] + rc["iters_s2"])
             warm.append(rw["iters_s1"] + rw["iters_s2"])
     assert np.mean(warm) < np.mean(cold), (cold, warm)
+
+
+def test_fit_warm_fallback_rule_runs_in_the_library(tomo):
+    """tomo_fit_warm: the library starts from the network's Theta0 exactly when
+    f(Theta0) < f(1/N) and otherwise from 1/N (for an untrained network whose
+    parameters are all zero, Theta0 is uniform up to float rounding), reaches
+    the cold fit's optimum either way, and refuses a handle whose shape does
+    not match the plan."""
+    D, M, X, C0 = 256, 128, 96.0, 16
+    lam = workloads.probe_intensities(D, X)
+    F = workloads.dense_poisson(M, lam)
+    kw = dict(F=F, M=M, D=D, X=X, bins_range=(4, 15), C0=C0)
+    Ptr, Ttr, nctr, _ = workloads.c5_batch(range(0, 96), **kw)
+    _, _, _, wte = workloads.c5_batch(range(20000, 20002), **kw)
+    shape = ows.Shape(D=D, C0=C0, M=M, C1=8, C2=8, K=5, S1=2, S2=4, H=16)
+
+    def check(ws, w):
+        with tomo.Plan.from_workload(w, precision="fp32") as pl:
+            P = dev(w.P)
+            Thc, rc = pl.fit(P, eps_kkt=1e-10, max_newton=2000)
+            Thw, rw, used = tomo.fit_warm(pl, ws, P, eps_kkt=1e-10, max_newton=2000)
+            uni = torch.full((w.M, w.N), 1.0 / w.N, dtype=torch.float64, device="cuda")
+            assert used == (pl.objective(P, ws.infer(P)) < pl.objective(P, uni))
+            if not used:
+                # the cold path is the plain fit, bit for bit
+                assert torch.equal(Thw, Thc)
+            fc, fw = pl.objective(P, Thc), pl.objective(P, Thw)
+            assert abs(fw - fc) <= 1e-7 * fc, (fc, fw)
+        return used
+
+    with make_ws(tomo, shape, 32, seed=11) as ws:
+        ws.set_params(np.zeros(ws.param_count, dtype=np.float32))
+        check(ws, wte[0])
+        Ptr_d, Ttr_d = dev(Ptr), dev(Ttr)
+        rng = np.random.default_rng(1)
+        for _ in range(300):
+            idx = rng.choice(len(nctr), 32, replace=False)
+            ws.train_step(Ptr_d[idx].contiguous(), Ttr_d[idx].contiguous(), nctr[idx], lr=3e-3)
+        for w in wte:
+            check(ws, w)
+    other = ows.Shape(D=D, C0=C0, M=M // 2, C1=4, C2=4, K=3, S1=2, S2=2, H=4)
+    with make_ws(tomo, other, 4) as ws2:
+        w = wte[0]
+        with tomo.Plan.from_workload(w, precision="fp32") as pl:
+            with pytest.raises(tomo.TomoError) as e:
+                tomo.fit_warm(pl, ws2, dev(w.P))
+            assert e.value.status == 1
