@@ -361,7 +361,11 @@ tomo_status tomo_ws_train_step(tomo_ws_t ws, const double *P, const double *T, c
  * N <= C0 columns, unpadded): every row on the simplex. */
 tomo_status tomo_ws_infer(tomo_ws_t ws, const double *P, int64_t N, double *Theta0);
 /* Algorithm 3 started from the learned warm start, with its fallback: Theta0
- * = tomo_ws_infer(ws, P, N); when f(Theta0) < f(1/N) (both evaluated in
+ * = tomo_ws_infer(ws, P, N); with zero_below > 0, the entries of each row of
+ * Theta0 below zero_below x the row's largest are set to 0 and the row is
+ * rescaled to sum 1 (a softmax has no exact zeros, while most entries of a
+ * detector POVM are zero at the optimum: the zeros start at their bound);
+ * zero_below = 0 keeps the network's output.  When f(Theta0) < f(1/N) (both evaluated in
  * double, Eq. min + Eq. regul) the fit starts from Theta0 (warm_start = 1),
  * else from Theta = 1/N; a warm-started fit that fails (any status other
  * than TOMO_OK and TOMO_ENOTCONV, or a non-finite objective) is redone from
@@ -371,7 +375,8 @@ tomo_status tomo_ws_infer(tomo_ws_t ws, const double *P, int64_t N, double *Thet
  * receives 1 when the returned Theta comes from the warm-started fit.  The
  * paper has no counterpart (it starts from 1/N). */
 tomo_status tomo_fit_warm(tomo_plan_t plan, tomo_ws_t ws, const double *P, double *Theta,
-                          const tomo_fit_opts *opts, tomo_fit_report *report, int32_t *used_warm);
+                          double zero_below, const tomo_fit_opts *opts, tomo_fit_report *report,
+                          int32_t *used_warm);
 
 /* Parameter file: magic "TOMOWS01", the nine shape fields, the floats. */
 tomo_status tomo_ws_save(tomo_ws_t ws, const char *path);

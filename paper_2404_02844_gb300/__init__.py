@@ -114,7 +114,7 @@ EXPORTS = [
     ("tomo_ws_train_step", c_i32, [c_ptr, c_ptr, c_ptr, c_ptr, c_i32, ctypes.c_float,
                                    ctypes.POINTER(ctypes.c_float)]),
     ("tomo_ws_infer", c_i32, [c_ptr, c_ptr, c_i64, c_ptr]),
-    ("tomo_fit_warm", c_i32, [c_ptr, c_ptr, c_ptr, c_ptr, ctypes.POINTER(tomo_fit_opts),
+    ("tomo_fit_warm", c_i32, [c_ptr, c_ptr, c_ptr, c_ptr, c_dbl, ctypes.POINTER(tomo_fit_opts),
                               ctypes.POINTER(tomo_fit_report), ctypes.POINTER(c_i32)]),
     ("tomo_ws_save", c_i32, [c_ptr, ctypes.c_char_p]),
     ("tomo_ws_load", c_i32, [c_ptr, ctypes.c_char_p]),
@@ -540,11 +540,13 @@ class WarmStart:
         _check(lib().tomo_ws_load(self._h, str(path).encode()), "tomo_ws_load")
 
 
-def fit_warm(plan, ws, P, **opts):
+def fit_warm(plan, ws, P, zero_below=0.0, **opts):
     """tomo_fit_warm: Algorithm 3 started from the learned Theta0, falling
     back to 1/N when f(Theta0) >= f(1/N) or when the warm-started fit fails
-    (the rule runs in the library).  P: float64 CUDA tensor.  Returns (Theta,
-    report, used_warm_start)."""
+    (the rule runs in the library); zero_below > 0 first sets the entries of
+    each row of Theta0 below zero_below x the row's largest to 0 and rescales
+    the row.  P: float64 CUDA tensor.  Returns (Theta, report,
+    used_warm_start)."""
     import torch
     o = tomo_fit_opts_default()
     for k, v in opts.items():
@@ -554,7 +556,7 @@ def fit_warm(plan, ws, P, **opts):
     Th = torch.empty(plan.M, plan.N, dtype=torch.float64, device="cuda")
     rep = tomo_fit_report()
     used = c_i32(0)
-    st = lib().tomo_fit_warm(plan._h, ws._h, _ptr(P), _ptr(Th), ctypes.byref(o), ctypes.byref(rep),
+    st = lib().tomo_fit_warm(plan._h, ws._h, _ptr(P), _ptr(Th), float(zero_below), ctypes.byref(o), ctypes.byref(rep),
                              ctypes.byref(used))
     _check(st, "tomo_fit_warm", allow=(0, 4))
     d = _fit_dict(rep)

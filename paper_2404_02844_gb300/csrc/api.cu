@@ -1064,13 +1064,15 @@ tomo_status tomo_fit(tomo_plan_t plan, const double *P, double *Theta, const tom
 }
 
 tomo_status tomo_fit_warm(tomo_plan_t plan, tomo_ws_t ws, const double *P, double *Theta,
-                          const tomo_fit_opts *opts, tomo_fit_report *report, int32_t *used_warm)
+                          double zero_below, const tomo_fit_opts *opts, tomo_fit_report *report,
+                          int32_t *used_warm)
 {
     Plan *pp = reinterpret_cast<Plan *>(plan);
     if (used_warm) *used_warm = 0;
     if (!pp || !ws || !P || !Theta) return fail(TOMO_EINVAL, "NULL argument");
     Plan &p = *pp;
     int64_t wD = 0, wM = 0, wC0 = 0;
+    if (!(zero_below >= 0.0 && zero_below < 1.0)) return fail(TOMO_EINVAL, "zero_below must lie in [0, 1)");
     if (!ws_shape(ws, &wD, &wM, &wC0) || wD != p.D || wM != p.M || p.N > wC0)
         return fail(TOMO_EINVAL, "the warm-start handle does not match the plan (D, M, N <= C0)");
     if (!is_device_pointer(P) || !is_device_pointer(Theta))
@@ -1080,6 +1082,7 @@ tomo_status tomo_fit_warm(tomo_plan_t plan, tomo_ws_t ws, const double *P, doubl
     const int64_t MN = p.M * p.N;
     // Theta0 from the network, then f(Theta0) and f(1/N) in double
     TOMO_TRY(tomo_ws_infer(ws, P, p.N, Theta));
+    if (zero_below > 0.0) CUDA_TRY(launch_zero_small_rows(p, Theta, zero_below));
     double f0 = 0.0, fu = 0.0;
     TOMO_TRY(residual_objective(p, P, Theta, p.R, &f0));
     CUDA_TRY(launch_fill(p, p.Th, 1.0 / double(p.N), MN));

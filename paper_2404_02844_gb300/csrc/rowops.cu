@@ -117,6 +117,37 @@ __device__ __forceinline__ void store_row(double *dst, int64_t i, int64_t N, int
 #define ROW_LOOP_END }
 
 // ---------------------------------------------------------------------------
+// Sparsified start of a warm-started fit: in every row the entries below rel
+// x the row's largest become 0 and the row is rescaled to sum 1 (rows of a
+// softmax have no exact zeros).  Warp per row.
+// ---------------------------------------------------------------------------
+template <int VPL>
+__global__ void k_zero_small_rows(RowArgs a, double *X, double rel)
+{
+    ROW_LOOP_BEGIN
+    double x[VPL];
+    load_row<VPL>(X, i, a.N, lane, x);
+    double mx = 0.0;
+#pragma unroll
+    for (int k = 0; k < VPL; ++k) mx = fmax(mx, x[k]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < VPL; ++k) {
+        if (x[k] < rel * mx) x[k] = 0.0;
+        s += x[k];
+    }
+    s = warp_sum(s);
+    if (s > 0.0) {
+#pragma unroll
+        for (int k = 0; k < VPL; ++k) x[k] /= s;
+        store_row<VPL>(X, i, a.N, lane, x);
+    }
+    ROW_LOOP_END
+}
+
+// ---------------------------------------------------------------------------
 // Projection of every row onto the simplex (Eq. Mp1_proj).
 // ---------------------------------------------------------------------------
 template <int VPL>
@@ -809,6 +840,13 @@ cudaError_t launch_nonfinite_check(Plan &p, const double *x, int64_t n, int)
     return cudaGetLastError();
 }
 
+cudaError_t launch_zero_small_rows(Plan &p, double *X, double rel)
+{
+    RowArgs a = row_args(p);
+    VPL_DISPATCH(p.N, k_zero_small_rows, row_grid(p), a, X, rel);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_project_rows(Plan &p, const double *X, double *Y)
 {
     RowArgs a = row_args(p);
@@ -858,12 +896,8 @@ cudaError_t launch_cg_update_xr(Plan &p, int stage)
     if (p.cg_f32 && (p.N % 4) == 0) {
         auto f4 = [](double *b) { return reinterpret_cast<float4 *>(b); };
         const int64_t cpl = (p.N / 4 + 31) / 32;
-        if (cpl <= 1)
-            k_cg_update_xr_f4<1><<<row_grid(p), ROW_WARPS * 32, 0, p.stream>>>(a, stage, p.freem, f4(p.p), f4(p.q), f4(p.x), f4(p.r), f4(p.z));
-        else if (cpl <= 2)
-            k_cg_update_xr_f4<2><<<row_grid(p), ROW_WARPS * 32, 0, p.stream>>>(a, stage, p.freem, f4(p.p), f4(p.q), f4(p.x), f4(p.r), f4(p.z));
-        else
-            k_cg_update_xr_f4<8><<<row_grid(p), ROW_WARPS * 32, 0, p.stream>>>(a, stage, p.freem, f4(p.p), f4(p.q), f4(p.x), f4(p.r), f4(p.z));
+        auto kern = cpl <= 1 ? k_cg_update_xr_f4<1> : cpl <= 2 ? k_cg_update_xr_f4<2> : k_cg_update_xr_f4<8>;
+        kern<<<row_grid(p), ROW_WARPS * 32, 0, p.stream>>>(a, stage, p.freem, f4(p.p), f4(p.q), f4(p.x), f4(p.r), f4(p.z));
         count_launch();
         return cudaGetLastError();
     }

@@ -159,6 +159,8 @@ cudaError_t launch_adjoint(Plan &p, int prec, AdjMode mode, const double *Y, dou
 cudaError_t launch_fill(Plan &p, double *x, double v, int64_t n);
 cudaError_t launch_regulariser(Plan &p, const double *X);   // -> sc->regval
 cudaError_t launch_project_rows(Plan &p, const double *X, double *Y);
+// X_{i,n} < rel * max_n X_{i,n} -> 0, then each row rescaled to sum 1 (in place)
+cudaError_t launch_zero_small_rows(Plan &p, double *X, double rel);
 cudaError_t launch_kkt(Plan &p, const double *Th, const double *G);  // -> sc->kkt2
 cudaError_t launch_setup1(Plan &p, int stage, double eps_bar);  // kkt2, w2, eps, g, var, mrow
 cudaError_t launch_setup2(Plan &p, int stage, int max_cg, double eta_max, double eta_pow);  // I mask, CG start
@@ -213,5 +215,6 @@ tomo_status tomo_set_error(tomo_status s, const char *msg);
 
 // kernel launch accounting (all threads)
 void count_launch(int n = 1);
+
 
 }  // namespace tomo

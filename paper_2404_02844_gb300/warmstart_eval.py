@@ -45,6 +45,9 @@ def main():
     ap.add_argument("--fit-seconds", type=float, default=60.0, help="wall-clock bound of every evaluation fit")
     ap.add_argument("--label-newton", type=int, default=1000, help="Newton cap of the label solves")
     ap.add_argument("--save", default=None)
+    ap.add_argument("--load", default=None, help="parameter file: skip the labels and the training")
+    ap.add_argument("--zero-below", default="0",
+                    help="comma-separated sparsification thresholds of Theta0 to compare")
     args = ap.parse_args()
 
     import torch
@@ -62,8 +65,8 @@ def main():
     t_data = time.perf_counter() - t0
     Ptr_d = torch.from_numpy(Ptr).cuda()
     Ttr_d = torch.from_numpy(Ttr).cuda()
-    label_info = {"labels": args.labels}
-    if args.labels == "solver":
+    label_info = {"labels": args.labels if not args.load else f"loaded {args.load}"}
+    if args.labels == "solver" and not args.load:
         # targets = the solver's optima of the training instances (batched)
         t0 = time.perf_counter()
         problems, outs = [], []
@@ -95,19 +98,24 @@ def main():
     Pte_d = torch.from_numpy(Pte[:args.batch]).cuda()
     Tte_d = torch.from_numpy(Tte[:args.batch]).cuda()
     l_test0, _ = ws.loss_grad(Pte_d, Tte_d, ncte[:args.batch])
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    losses = []
-    for s in range(args.steps):
-        idx = torch.from_numpy(rng.choice(args.train, args.batch, replace=False)).cuda()
-        losses.append(ws.train_step(Ptr_d[idx].contiguous(), Ttr_d[idx].contiguous(),
-                                    nctr[idx.cpu().numpy()], lr=args.lr))
-    torch.cuda.synchronize()
-    t_train = time.perf_counter() - t0
+    losses, t_train = [float("nan")], 0.0
+    if args.load:
+        ws.load(args.load)
+    else:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        losses = []
+        for s in range(args.steps):
+            idx = torch.from_numpy(rng.choice(args.train, args.batch, replace=False)).cuda()
+            losses.append(ws.train_step(Ptr_d[idx].contiguous(), Ttr_d[idx].contiguous(),
+                                        nctr[idx.cpu().numpy()], lr=args.lr))
+        torch.cuda.synchronize()
+        t_train = time.perf_counter() - t0
     l_test1, _ = ws.loss_grad(Pte_d, Tte_d, ncte[:args.batch])
     if args.save:
         ws.save(args.save)
 
+    zbs = [float(z) for z in args.zero_below.split(",")]
     rows = []
     for w in wte:
         with tomo.Plan.from_workload(w, precision=args.precision) as pl:
@@ -120,22 +128,35 @@ def main():
             Thc, rc = pl.fit(P, f_target=target, eps_kkt=0.0, max_newton=3000, max_seconds=args.fit_seconds)
             torch.cuda.synchronize()
             tc = time.perf_counter() - t0
-            t0 = time.perf_counter()
-            Thw, rw, used = tomo.fit_warm(pl, ws, P, f_target=target, eps_kkt=0.0, max_newton=3000,
-                                          max_seconds=args.fit_seconds)
-            torch.cuda.synchronize()
-            tw = time.perf_counter() - t0
-            fc, fw = pl.objective(P, Thc), pl.objective(P, Thw)
+            fc = pl.objective(P, Thc)
             uni = torch.full((w.M, w.N), 1.0 / w.N, dtype=torch.float64, device="cuda")
             f0w, f0u = pl.objective(P, ws.infer(P)), pl.objective(P, uni)
-        rows.append(dict(N=w.N, cold_iters=rc["iters_s1"] + rc["iters_s2"],
-                         warm_iters=rw["iters_s1"] + rw["iters_s2"], cold_s=tc, warm_s=tw,
-                         cold_stop=rc["stop_name"], warm_stop=rw["stop_name"],
-                         used_warm=bool(used), rel_gap_cold=(fc - rref["f"]) / rref["f"],
-                         rel_gap_warm=(fw - rref["f"]) / rref["f"], f0_warm_over_uniform=f0w / f0u))
-        print(json.dumps({"test": len(rows), **rows[-1]}), flush=True)
+            row = dict(N=w.N, cold_iters=rc["iters_s1"] + rc["iters_s2"], cold_s=tc,
+                       cold_stop=rc["stop_name"], rel_gap_cold=(fc - rref["f"]) / rref["f"],
+                       f0_warm_over_uniform=f0w / f0u, warm={})
+            for zb in zbs:
+                t0 = time.perf_counter()
+                Thw, rw, used = tomo.fit_warm(pl, ws, P, zero_below=zb, f_target=target, eps_kkt=0.0,
+                                              max_newton=3000, max_seconds=args.fit_seconds)
+                torch.cuda.synchronize()
+                tw = time.perf_counter() - t0
+                fw = pl.objective(P, Thw)
+                row["warm"][repr(zb)] = dict(iters=rw["iters_s1"] + rw["iters_s2"], s=tw, stop=rw["stop_name"],
+                                             used_warm=bool(used), rel_gap=(fw - rref["f"]) / rref["f"])
+        rows.append(row)
+        print(json.dumps({"test": len(rows), **row}), flush=True)
     ci = np.array([r["cold_iters"] for r in rows])
-    wi = np.array([r["warm_iters"] for r in rows])
+    cs = np.array([r["cold_s"] for r in rows])
+    warm = {}
+    for zb in zbs:
+        k = repr(zb)
+        wi = np.array([r["warm"][k]["iters"] for r in rows])
+        wsec = np.array([r["warm"][k]["s"] for r in rows])
+        warm[k] = {"iters_mean": float(wi.mean()), "s_mean": float(wsec.mean()),
+                   "s_median": float(np.median(wsec)), "s_total": float(wsec.sum()),
+                   "faster_fraction": float(np.mean(wsec < cs)),
+                   "used_warm": int(sum(r["warm"][k]["used_warm"] for r in rows)),
+                   "max_rel_gap": float(max(r["warm"][k]["rel_gap"] for r in rows))}
     out = {
         "workload": "warm-start population: M=1024 D=2048 lambda lin [0,768], bins U{16..63}, "
                     "eta U[0.3,0.95], crosstalk U[0,1e-2], dark U[0,1e-3], 1e6 shots, gamma 1e-3",
@@ -144,14 +165,10 @@ def main():
         "loss_first": losses[0], "loss_last_100": float(np.mean(losses[-100:])),
         "heldout_loss_before": l_test0, "heldout_loss_after": l_test1,
         "precision": args.precision, "test_instances": args.test,
-        "cold_iters_mean": float(ci.mean()), "warm_iters_mean": float(wi.mean()),
-        "cold_s_mean": float(np.mean([r["cold_s"] for r in rows])),
-        "warm_s_mean": float(np.mean([r["warm_s"] for r in rows])),
-        "cold_s_median": float(np.median([r["cold_s"] for r in rows])),
-        "warm_s_median": float(np.median([r["warm_s"] for r in rows])),
-        "warm_faster_fraction": float(np.mean([r["warm_s"] < r["cold_s"] for r in rows])),
-        "used_warm": int(sum(r["used_warm"] for r in rows)),
-        "max_rel_gap": float(max(max(r["rel_gap_cold"], r["rel_gap_warm"]) for r in rows)),
+        "cold_iters_mean": float(ci.mean()), "cold_s_mean": float(cs.mean()),
+        "cold_s_median": float(np.median(cs)), "cold_s_total": float(cs.sum()),
+        "max_rel_gap_cold": float(max(r["rel_gap_cold"] for r in rows)),
+        "warm_by_zero_below": warm,
         **label_info,
         "f0_warm_over_uniform_median": float(np.median([r["f0_warm_over_uniform"] for r in rows])),
         "rows": rows,

@@ -302,6 +302,16 @@ def test_fit_c2_full_size(tomo, prec):
     Th = host(Th)
     assert np.abs(Th.sum(1) - 1).max() <= 1e-13 * w.N
     assert Th.min() >= 0.0
+    # Theta against the certified optimum on the stored rows, element by
+    # element: tau_Theta is 10 x what the oracle's own solve differs from
+    # Theta* at the same objective gap (tests/golden/make_fstar.py
+    # --theta-tol); Theta is poorly determined along the flat directions, so
+    # the tolerance is calibrated, not fixed
+    if "theta_tol" in gold:
+        rows = np.array(gold["sample_rows"])
+        diff = np.abs(Th[rows] - np.array(gold["theta_rows"]))
+        tol = gold["theta_tol"]
+        assert diff.max() <= tol, (prec, diff.max(), int(rows[np.argmax(diff.max(1))]), tol)
 
 
 def test_c3_scale_products_on_sampled_rows(tomo):
@@ -492,3 +502,34 @@ def test_bounded_tensor_core_waits_report_a_timeout_and_leave_the_plan_usable(to
         assert rep["status"] == "TOMO_OK", rep
     with tomo.Plan.from_workload(w, precision="fp32") as pl:
         assert tomo.lib().tomo_selftest_tc_timeout(pl._h) == 1   # EINVAL: not the tensor-core form
+
+
+@pytest.mark.parametrize("prec", ["tc", "fp32"])
+def test_fit_batched_largest_c4_instance_reaches_the_oracle_optimum(tomo, prec):
+    """The corner of the batched distribution (instance 178: M = 8063, N =
+    127, D = 16126): solved in one batched call at every regularisation weight
+    for which the oracle's own solve converged (tests/golden/make_fstar_c4.py),
+    each result within 1e-8 of the oracle's optimum and on the simplices."""
+    path = os.path.join(GOLD, "fstar_c4_178.json")
+    if not os.path.exists(path):
+        pytest.skip("oracle optima of c4 instance 178 not generated")
+    with open(path) as fh:
+        gold = json.load(fh)
+    conv = [r for r in gold["results"].values() if r["converged"]]
+    assert conv, "no converged oracle solve recorded"
+    w = workloads.config_c4_instance(gold["instance"])
+    assert (w.M, w.N, w.D) == (gold["M"], gold["N"], gold["D"])
+    P = dev(w.P)
+    problems, thetas = [], []
+    for r in conv:
+        Th = torch.empty(w.M, w.N, dtype=torch.float64, device="cuda")
+        problems.append((w.M, w.N, w.lam, w.band_k, r["gamma"], P, Th))
+        thetas.append(Th)
+    sts, reps = tomo.fit_batched(problems, precision=prec, concurrency=len(problems),
+                                 f_target=0.0, eps_kkt=1e-10, max_newton=3000)
+    for r, Th, st, rep in zip(conv, thetas, sts, reps):
+        pr = oracle.Problem(w.M, w.N, w.lam, w.band_k, r["gamma"])
+        f = pr.objective(w.P, host(Th))
+        assert (f - r["f"]) / r["f"] <= 1e-8, (r["gamma"], f, r["f"], rep)
+        T = host(Th)
+        assert np.abs(T.sum(1) - 1).max() <= 1e-12 and T.min() >= 0.0

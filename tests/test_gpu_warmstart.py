@@ -179,6 +179,13 @@ def test_fit_warm_fallback_rule_runs_in_the_library(tomo):
                 assert torch.equal(Thw, Thc)
             fc, fw = pl.objective(P, Thc), pl.objective(P, Thw)
             assert abs(fw - fc) <= 1e-7 * fc, (fc, fw)
+            # the sparsified start (small entries of Theta0 set to their bound)
+            # goes through the same rule and reaches the same optimum
+            Ths, rs, _ = tomo.fit_warm(pl, ws, P, zero_below=1e-3, eps_kkt=1e-10, max_newton=2000)
+            T = Ths.cpu().numpy()
+            assert np.abs(T.sum(1) - 1).max() <= 1e-12 and T.min() >= 0.0
+            fs = pl.objective(P, Ths)
+            assert abs(fs - fc) <= 1e-7 * fc, (fc, fs)
         return used
 
     with make_ws(tomo, shape, 32, seed=11) as ws:
@@ -197,4 +204,10 @@ def test_fit_warm_fallback_rule_runs_in_the_library(tomo):
         with tomo.Plan.from_workload(w, precision="fp32") as pl:
             with pytest.raises(tomo.TomoError) as e:
                 tomo.fit_warm(pl, ws2, dev(w.P))
+            assert e.value.status == 1
+    with make_ws(tomo, shape, 4) as ws3:
+        w = wte[0]
+        with tomo.Plan.from_workload(w, precision="fp32") as pl:
+            with pytest.raises(tomo.TomoError) as e:
+                tomo.fit_warm(pl, ws3, dev(w.P), zero_below=1.5)
             assert e.value.status == 1
