@@ -38,6 +38,10 @@ def main():
                     help="> 0: time one-at-a-time solves on the first K problems only "
                          "(the full serial pass is skipped)")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--fit-seconds", type=float, default=0.0,
+                    help="> 0: wall-clock bound of every solve")
+    ap.add_argument("--data-workers", type=int, default=1,
+                    help="host processes that generate the instances (spawned before any GPU call)")
     args = ap.parse_args()
 
     import torch
@@ -48,8 +52,17 @@ def main():
 
     build.build()
     t0 = time.perf_counter()
-    inst = W.config_c4(n_instances=args.instances, max_M=args.max_m)
+    if args.data_workers > 1:
+        import multiprocessing as mp
+        from concurrent.futures import ProcessPoolExecutor
+        with ProcessPoolExecutor(args.data_workers, mp_context=mp.get_context("spawn")) as ex:
+            inst = list(ex.map(W.config_c4_instance, range(args.instances),
+                               [args.max_m] * args.instances))
+    else:
+        inst = W.config_c4(n_instances=args.instances, max_M=args.max_m)
     t_data = time.perf_counter() - t0
+    print(json.dumps({"data_s": t_data}), flush=True)
+    lim = dict(max_seconds=args.fit_seconds) if args.fit_seconds > 0 else {}
     problems = [(w, g) for w in inst for g in W.C4_GAMMAS]
     Ps = [torch.from_numpy(w.P).cuda() for w, _ in problems]
 
@@ -59,7 +72,7 @@ def main():
         torch.cuda.synchronize()
         t = time.perf_counter()
         st, reps = tomo.fit_batched(probs, precision=args.precision, concurrency=conc, autotune=autotune,
-                                    eps_kkt=args.eps_kkt, max_newton=args.max_newton)
+                                    eps_kkt=args.eps_kkt, max_newton=args.max_newton, **lim)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t
         return dt, st, reps
@@ -84,7 +97,10 @@ def main():
         out[key] = {"seconds": dt, "solves_per_s": len(problems) / dt,
                     "newton_iters": int(sum(r["iters_s1"] + r["iters_s2"] for r in reps)),
                     "cg_products": int(sum(r["cg_total"] for r in reps)),
-                    "statuses": sorted(set(int(s) for s in st))}
+                    "statuses": sorted(set(int(s) for s in st)),
+                    "stops": {k: int(v) for k, v in zip(*np.unique([r["stop_name"] for r in reps],
+                                                                    return_counts=True))},
+                    "kkt_max": float(max(r["kkt"] for r in reps))}
         print(json.dumps({key: out[key]}), flush=True)
     ref = fs[f"conc{args.concurrency}_default"]
     if args.serial_sample > 0:
@@ -98,7 +114,7 @@ def main():
         torch.cuda.synchronize()
         t = time.perf_counter()
         st, reps = tomo.fit_batched(probs, precision=args.precision, concurrency=1,
-                                    eps_kkt=args.eps_kkt, max_newton=args.max_newton)
+                                    eps_kkt=args.eps_kkt, max_newton=args.max_newton, **lim)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t
         fk = np.array([r["f"] for r in reps])
