@@ -20,9 +20,13 @@ if ROOT not in sys.path:
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3s"],
-                    help="c3s: the megascale geometry at 1/8 size (M = D = 131072, N = 100, "
-                         "lambda linear in [0, 0.9 M], band +-10 sqrt(lambda); products only)")
+    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "c3s", "f2"],
+                    help="c3: the megascale geometry (M = D = 1e6, N = 100, lambda linear in "
+                         "[0, 9e5], band +-10 sqrt(lambda); products only, timed with CUDA events); "
+                         "c3s: the same geometry at 1/8 size (M = D = 131072, N = 100, "
+                         "lambda linear in [0, 0.9 M], band +-10 sqrt(lambda); products only); "
+                         "f2: the loop detector at the paper's size (M = 1210581, N = 151, "
+                         "D = 1076, lambda_d = d^2, gamma 1e-5)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "mixed", "tc"])
     ap.add_argument("--newton", type=int, default=3)
     ap.add_argument("--op", default="fit", choices=["fit", "hvp", "fwd", "adj"],
@@ -40,8 +44,8 @@ def main():
     from paper_2404_02844_gb300 import build
 
     build.build()
-    if args.config == "c3s":
-        M = D = 131072
+    if args.config in ("c3", "c3s"):
+        M = D = 1_000_000 if args.config == "c3" else 131072
         N = 100
         lam = workloads.probe_intensities(D, 0.9 * M)
         with tomo.Plan(M, N, lam, 10.0, 1e-3, precision=args.precision) as pl:
@@ -49,13 +53,16 @@ def main():
             X = torch.rand(M, N, dtype=torch.float64, device="cuda", generator=g)
             pl.hvp(X)
             torch.cuda.synchronize()
-            t0 = time.perf_counter()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record()
             for _ in range(args.reps):
                 pl.hvp(X)
+            ev1.record()
             torch.cuda.synchronize()
-            print(f"c3s {args.precision}: {args.reps} x hvp, {(time.perf_counter() - t0) / args.reps * 1e3:.3f} ms each")
+            print(f"{args.config} {args.precision}: {args.reps} x hvp, {ev0.elapsed_time(ev1) / args.reps:.3f} ms each")
         return
-    w = {"c1": workloads.config_c1, "c2": workloads.config_c2}[args.config]()
+    w = {"c1": workloads.config_c1, "c2": workloads.config_c2,
+         "f2": lambda: workloads.config_f2(M=1210581, D=1076, gamma=1e-5)}[args.config]()
     P = torch.from_numpy(w.P).cuda()
     with tomo.Plan.from_workload(w, precision=args.precision) as pl:
         if args.op != "fit":
