@@ -10,22 +10,24 @@
 // Operands are bf16 in shared memory, K-major, 128-byte swizzled; the
 // accumulator is f32 in tensor memory.  Precision is recovered by splitting
 // every operand into hi + lo bf16 parts and accumulating hi*hi + hi*lo +
-// lo*hi (three MMAs per K slice, ~17 significant bits: the dropped lo*lo
-// term is of the order of what the two-part split itself leaves, 2^-18).
+// lo*hi (three MMAs per K step of 16 into one accumulator, ~17 significant
+// bits: the dropped lo*lo term is of the order of what the two-part split
+// itself leaves, 2^-18).
 //
 // The contraction kernel is warp-specialised and persistent (one CTA per SM,
 // a list of work units each):
-//   producer warps 0-7  generate the Poisson weights of every 64-wide slice
+//   producer warps 0-15 generate the Poisson weights of every 64-wide slice
 //                       straight into a ring of A stages (runs of 8 photon
 //                       numbers from the log-space anchors, exact ratio
 //                       recurrence in float) and signal them on an mbarrier;
-//   warp 8              loads the vector operand of each slice by TMA from a
-//                       transposed bf16 hi/lo copy (rows = outcomes,
-//                       contiguous along the reduction index), issues the
-//                       slice's MMAs into one of two tensor-memory
+//   warp 16             issues the slice's MMAs into one of two tensor-memory
 //                       accumulators and commits them to the barriers that
 //                       free the stages and publish a finished unit;
-//   warps 9-12          move each finished accumulator to the unit's f32
+//   warp 17             loads the vector operand of each slice by TMA from a
+//                       transposed bf16 hi/lo copy (rows = outcomes,
+//                       contiguous along the reduction index), up to three
+//                       slices ahead of the MMAs;
+//   warps 18-21         move each finished accumulator to the unit's f32
 //                       partial tile (column-major, coalesced stores) while
 //                       the MMAs of the next unit run in the other one.
 // The reduction range of every tile is cut into work units (split-K, planned
@@ -48,11 +50,12 @@ namespace tomo {
 constexpr int TC_BK = 64;            // reduction slice per stage (one 128-byte bf16 row)
 constexpr int TC_SA = 3;             // A (weight) stages
 constexpr int TC_SB = 3;             // B (vector) stages, filled by TMA
-constexpr int TC_PROD = 256;         // producer threads (warps 0-7)
-constexpr int TC_MMA_WARP = 8;
-constexpr int TC_THREADS = 13 * 32;
+constexpr int TC_PROD = 512;         // producer threads (warps 0-15)
+constexpr int TC_MMA_WARP = 16;      // MMA issue
+constexpr int TC_TMA_WARP = 17;      // TMA of the vector operand
+constexpr int TC_THREADS = 22 * 32;  // + epilogue warps 18-21
 constexpr uint32_t TC_WAIT_LIMIT = 1u << 24;
-constexpr int TC_WIN = 3;            // windows of the per-slice tables (loaded two slices ahead)
+constexpr int TC_WIN = 4;            // windows of the per-slice tables (filled three slices ahead)
 static_assert(TC_SA == TC_SB, "the B copy of slice g + 2 reuses the stage of slice g - 1");
 
 template <int BN>
@@ -70,8 +73,9 @@ struct TcLayout {
     static constexpr int NBARS = 2 * TC_SA + TC_SB + 4;              // a_full, a_empty, b_full, acc_full[2], acc_empty[2]
     static constexpr int CTRL_BYTES = NBARS * 8 + 16;                // + tensor-memory holder, abort flag
     static constexpr int TOTAL = 1024 + BAR_OFF + CTRL_BYTES;
-    static constexpr int ACC_COLS = BN < 32 ? 32 : BN;               // one accumulator
-    static constexpr int TMEM_COLS = 2 * ACC_COLS;                   // two (power of two >= 32)
+    static constexpr int ACC_COLS = BN;                              // one accumulator (BN >= 32)
+    static constexpr int TMEM_COLS = 2 * ACC_COLS;                   // two, a power of two
+    static_assert(BN >= 32 && TMEM_COLS <= 512, "tensor memory");
     static_assert(TOTAL <= 227 * 1024, "shared memory per CTA");
     static_assert(B_OFF % 1024 == 0 && B_STAGE % 1024 == 0 && B_BYTES % 1024 == 0, "swizzle atoms");
 };
@@ -182,7 +186,7 @@ __device__ __forceinline__ void tc_expand_run(float v, float2 lam, int32_t lo, i
     }
 }
 
-// Barrier of the 256 producer threads (named barrier 1) that also returns
+// Barrier of the producer threads (named barrier 1) that also returns
 // the OR of their flags: every producer reaches it once per slice after
 // bounded waits only, so it cannot hold a producer forever.
 __device__ __forceinline__ bool producers_sync_or(bool v)
@@ -191,9 +195,9 @@ __device__ __forceinline__ bool producers_sync_or(bool v)
     asm volatile(
         "{\n\t.reg .pred pi, po;\n\t"
         "setp.ne.u32 pi, %1, 0;\n\t"
-        "bar.red.or.pred po, 1, 256, pi;\n\t"
+        "bar.red.or.pred po, 1, %2, pi;\n\t"
         "selp.u32 %0, 1, 0, po;\n\t}"
-        : "=r"(r) : "r"(uint32_t(v)) : "memory");
+        : "=r"(r) : "r"(uint32_t(v)), "n"(TC_PROD) : "memory");
     return r != 0;
 }
 
@@ -268,13 +272,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(const __grid_constant
 
     if (warp < TC_MMA_WARP) {
         // ------------------------------------------------------------ producers
-        // Per-slice tables live in shared memory, loaded two slices ahead by
-        // the first 64 producer threads: the forward's ratios 1/(i+1) of the
-        // slice's photon numbers, the adjoint's probe metadata of the slice's
-        // probes (its ratios cover the whole tile and are loaded per unit).
-        // Producer-wide agreement (tables written, a wait given up) goes
-        // through one bounded barrier with an OR reduction per slice.
-        constexpr int QRUNS = (TILE_R * TC_BK / RUN) / TC_PROD;       // 4 runs of 8 per thread
+        // Per-slice tables live in shared memory windows, filled three slices
+        // ahead by the first 64 producer threads with asynchronous copies (no
+        // register waits on the critical path): the forward's ratios 1/(i+1)
+        // of the slice's photon numbers, the adjoint's probe metadata of the
+        // slice's probes (its ratios cover the whole tile and are loaded per
+        // unit).  A copy group is committed every slice; waiting for all but
+        // the latest before the slice barrier publishes the tables of the next
+        // slice.  Producer-wide agreement (tables written, a wait given up)
+        // goes through one bounded barrier with an OR reduction per slice.
+        constexpr int QRUNS = (TILE_R * TC_BK / RUN) / TC_PROD;       // 2 runs of 8 per thread
+        static_assert(QRUNS * TC_PROD == TILE_R * TC_BK / RUN, "runs per producer");
         float *stg = staging + ((tid >> 3) * 8) * 9;
         float2 (*win_r)[TC_BK] = reinterpret_cast<float2 (*)[TC_BK]>(sm + L::TAB_OFF);
         ProbeMeta (*win_m)[TC_BK] = reinterpret_cast<ProbeMeta (*)[TC_BK]>(sm + L::TAB_OFF + TC_WIN * TC_BK * 8);
@@ -289,20 +297,31 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(const __grid_constant
             const int64_t r0 = int64_t(wu.tile) * TILE_R;
             // forward: every thread expands runs of one probe (row tid % 128)
             const ProbeMeta my = FWD ? load_meta(a, r0 + (tid % TILE_R)) : none;
-            // entry tid (< 64) of the table of slice j
-            auto load_tab = [&](int j, float2 &rv, ProbeMeta &mv) {
+            // entry tid (< 64) of the table of slice j, synchronously or by
+            // asynchronous copies (entries outside the range are written
+            // directly; the slot belongs to this thread alone)
+            auto put_tab = [&](int j, bool async) {
                 const int64_t k0j = int64_t(wu.k0) + int64_t(j) * TC_BK;
                 if (FWD) {
+                    float2 *dst = &win_r[j % TC_WIN][tid];
                     const int64_t idx = k0j + tid + 1;
-                    rv = idx <= a.M + RUN ? __ldg(&a.rinv2[idx]) : make_float2(0.f, 0.f);
+                    if (idx > a.M + RUN) *dst = make_float2(0.f, 0.f);
+                    else if (async) tc::cp_async<8>(dst, &a.rinv2[idx]);
+                    else *dst = __ldg(&a.rinv2[idx]);
                 } else {
+                    ProbeMeta *dst = &win_m[j % TC_WIN][tid];
                     const int64_t d = k0j + tid;
-                    mv = d < wu.k1 ? load_meta(a, d) : none;
+                    if (d >= wu.k1 || d >= a.D) {
+                        *dst = none;
+                    } else if (async) {
+                        tc::cp_async<4>(&dst->lo, &a.lo[d]);
+                        tc::cp_async<4>(&dst->hi, &a.hi[d]);
+                        tc::cp_async<8>(&dst->aoff, &a.aoff[d]);
+                        tc::cp_async<8>(&dst->lam, &a.lam2[d]);
+                    } else {
+                        *dst = load_meta(a, d);
+                    }
                 }
-            };
-            auto store_tab = [&](int j, const float2 &rv, const ProbeMeta &mv) {
-                if (FWD) win_r[j % TC_WIN][tid] = rv;
-                else win_m[j % TC_WIN][tid] = mv;
             };
             // the anchors of every run of slice j (tables of slice j in place)
             float anc[QRUNS];
@@ -320,19 +339,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(const __grid_constant
                     }
                 }
             };
-            {   // prologue of the unit: tables of slices 0 and 1, the adjoint's ratios
+            {   // prologue of the unit: tables of slices 0 to 2, the adjoint's ratios
                 // (after every producer is done with the previous unit's tables)
                 producers_sync_or(false);
-                float2 rv = make_float2(0.f, 0.f);
-                ProbeMeta mv = none;
-                if (tid < TC_BK) {
-                    load_tab(0, rv, mv);
-                    store_tab(0, rv, mv);
-                    if (nsteps > 1) {
-                        load_tab(1, rv, mv);
-                        store_tab(1, rv, mv);
-                    }
-                }
+                if (tid < TC_BK)
+                    for (int j = 0; j < 3 && j < nsteps; ++j) put_tab(j, false);
                 if (!FWD)
                     for (int k = tid; k < TILE_R + RUN; k += TC_PROD) {
                         const int64_t idx = r0 + k + 1;
@@ -345,16 +356,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(const __grid_constant
                 const int st = int(g % TC_SA);
                 bool wok = true;
                 if (g >= TC_SA) wok = warp_wait(&a_empty[st], ((g / TC_SA) - 1) & 1u, limit, abort_flag);
-                // every producer is past slice s - 1: the tables of slice s + 1
-                // are written and the window of slice s - 1 may be reused
+                // the tables of slice s + 1 (copies issued at slice s - 2) have
+                // landed; after the barrier every producer is past slice s - 1,
+                // so the window of slice s - 1 may take slice s + 3
+                if (tid < TC_BK) tc::cp_async_wait<1>();
                 if (producers_sync_or(!wok)) {
                     *abort_flag = 1;
                     ok = false;
                     break;
                 }
-                float2 rv = make_float2(0.f, 0.f);
-                ProbeMeta mv = none;
-                if (tid < TC_BK && s + 2 < nsteps) load_tab(s + 2, rv, mv);
+                if (tid < TC_BK) {
+                    if (s + 3 < nsteps) put_tab(s + 3, true);
+                    tc::cp_async_commit();
+                }
                 unsigned char *A_hi = sm + st * L::A_STAGE;
                 unsigned char *A_lo = A_hi + L::A_BYTES;
                 const int64_t k0 = int64_t(wu.k0) + int64_t(s) * TC_BK;
@@ -396,46 +410,29 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(const __grid_constant
                     *reinterpret_cast<uint4 *>(A_hi + tc::sw128_chunk(row, chunk)) = hi;
                     *reinterpret_cast<uint4 *>(A_lo + tc::sw128_chunk(row, chunk)) = lo;
                 }
-                if (tid < TC_BK && s + 2 < nsteps) store_tab(s + 2, rv, mv);
                 // the generic-proxy stores become visible to the tensor core
                 tc::fence_proxy_async_smem();
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(&a_full[st]);
             }
+            // no copy may still be in flight into a window the next unit's
+            // prologue rewrites
+            if (tid < TC_BK) tc::cp_async_wait<0>();
         }
+        if (tid < TC_BK) tc::cp_async_wait<0>();
     } else if (warp == TC_MMA_WARP) {
-        // ------------------------------------------- TMA of B, MMA issue (lane 0)
+        // --------------------------------------------------- MMA issue (lane 0)
         if (lane == 0) {
+            // hi*hi + hi*lo + lo*hi for each of the slice's four K steps of
+            // 16.  The stages sit at fixed strides, so a stage's operand
+            // descriptors are the first stage's plus a multiple of the stride
+            // (start-address field in 16-byte units; every shared-memory
+            // address is below 2^18 bytes, so the field never carries).
             constexpr uint32_t IDESC = tc::idesc_bf16_f32(TILE_R, BN);
-            // cursor over the CTA's slices in order, skipping empty units
-            struct Cur { int ui, s, ns; int64_t k0; };
-            auto seek = [&](Cur &c) {
-                while (c.ui < u_end) {
-                    const WorkUnit w = a.units[c.ui];
-                    c.ns = (w.k1 - w.k0) / TC_BK;
-                    c.k0 = w.k0;
-                    if (c.s < c.ns) return;
-                    ++c.ui;
-                    c.s = 0;
-                }
-            };
-            Cur tc_cur{u_begin, 0, 0, 0};
-            seek(tc_cur);
-            uint32_t issued = 0, consumed = 0;
-            int64_t last_commit = -1;
-            auto issue_b = [&](Cur &c) {
-                const int bs = int(issued % TC_SB);
-                unsigned char *B_hi = sm + L::B_OFF + bs * L::B_STAGE;
-                const int32_t x = int32_t(c.k0 + int64_t(c.s) * TC_BK);
-                tc::mbar_arrive_expect_tx(&b_full[bs], 2u * L::B_BYTES);
-                tc::tma_load_2d(B_hi, &a.tm_b_hi, x, int32_t(n0), &b_full[bs]);
-                tc::tma_load_2d(B_hi + L::B_BYTES, &a.tm_b_lo, x, int32_t(n0), &b_full[bs]);
-                ++issued;
-                ++c.s;
-                seek(c);
-            };
-            for (int j = 0; j < 2 && tc_cur.ui < u_end; ++j) issue_b(tc_cur);
+            const uint64_t da0 = tc::desc_kmajor_sw128(tc::smem_u32(sm));
+            const uint64_t db0 = tc::desc_kmajor_sw128(tc::smem_u32(sm + L::B_OFF));
             uint32_t g = 0, au = 0;
+            int64_t last_commit = -1;
             bool ok = true;
             for (int ui = u_begin; ui < u_end && ok; ++ui) {
                 const WorkUnit wu = a.units[ui];
@@ -449,34 +446,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(const __grid_constant
                 tc::tc_fence_after_sync();
                 const uint32_t d_tmem = tmem + uint32_t(acc * L::ACC_COLS);
                 for (int s = 0; s < nsteps; ++s, ++g) {
-                    const int st = int(g % TC_SA), bs = int(g % TC_SB);
-                    if (!tc::mbar_wait_or_abort(&b_full[bs], (g / TC_SB) & 1u, limit, abort_flag)) { ok = false; break; }
-                    ++consumed;
+                    const int st = int(g % TC_SA);
+                    if (!tc::mbar_wait_or_abort(&b_full[st], (g / TC_SB) & 1u, limit, abort_flag)) { ok = false; break; }
                     if (!tc::mbar_wait_or_abort(&a_full[st], (g / TC_SA) & 1u, limit, abort_flag)) { ok = false; break; }
                     tc::tc_fence_after_sync();
                     if (!a.skip_mma) {
-                        const uint32_t a_hi = tc::smem_u32(sm + st * L::A_STAGE), a_lo = a_hi + L::A_BYTES;
-                        const uint32_t b_hi = tc::smem_u32(sm + L::B_OFF + bs * L::B_STAGE), b_lo = b_hi + L::B_BYTES;
+                        const uint64_t ah = da0 + uint64_t(st) * uint64_t(L::A_STAGE >> 4);
+                        const uint64_t al = ah + uint64_t(L::A_BYTES >> 4);
+                        const uint64_t bh = db0 + uint64_t(st) * uint64_t(L::B_STAGE >> 4);
+                        const uint64_t bl = bh + uint64_t(L::B_BYTES >> 4);
 #pragma unroll
                         for (int kk = 0; kk < TC_BK / 16; ++kk) {
-                            const uint32_t off = kk * 32;   // 16 bf16 per MMA
-                            const uint32_t acc0 = (s > 0 || kk > 0) ? 1u : 0u;
-                            tc::mma_bf16(d_tmem, tc::desc_kmajor_sw128(a_hi + off), tc::desc_kmajor_sw128(b_hi + off), IDESC, acc0);
-                            tc::mma_bf16(d_tmem, tc::desc_kmajor_sw128(a_hi + off), tc::desc_kmajor_sw128(b_lo + off), IDESC, 1u);
-                            tc::mma_bf16(d_tmem, tc::desc_kmajor_sw128(a_lo + off), tc::desc_kmajor_sw128(b_hi + off), IDESC, 1u);
+                            const uint32_t acc0 = (s > 0 || kk > 0) ? 1u : 0u;   // 16 bf16 = 32 B per step
+                            tc::mma_bf16(d_tmem, ah + 2 * kk, bh + 2 * kk, IDESC, acc0);
+                            tc::mma_bf16(d_tmem, ah + 2 * kk, bl + 2 * kk, IDESC, 1u);
+                            tc::mma_bf16(d_tmem, al + 2 * kk, bh + 2 * kk, IDESC, 1u);
                         }
+                        // frees the A and the B stage of this slice
                         tc::mma_commit(&a_empty[st]);
                         last_commit = int64_t(g);
-                    }
-                    // the B copy of slice `issued` (= g + 2) reuses the stage of
-                    // slice g - 1: its MMAs must be complete
-                    if (tc_cur.ui < u_end) {
-                        if (g >= 1 && !tc::mbar_wait_or_abort(&a_empty[(g - 1) % TC_SA], ((g - 1) / TC_SA) & 1u,
-                                                              limit, abort_flag)) {
-                            ok = false;
-                            break;
-                        }
-                        issue_b(tc_cur);
                     }
                 }
                 if (!ok) break;
@@ -485,15 +473,43 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(const __grid_constant
             }
             if (!ok) {
                 *abort_flag = 1;
-                // nothing may still target this CTA's memory when it exits:
-                // the B copies issued but not consumed, and the last group of
-                // committed MMAs (its completion covers all earlier ones)
-                for (uint32_t j = consumed; j < issued; ++j)
-                    tc::mbar_wait_bounded(&b_full[j % TC_SB], (j / TC_SB) & 1u, limit);
+                // the last group of committed MMAs (its completion covers all
+                // earlier ones) must be done before tensor memory is freed
                 if (last_commit >= 0)
                     tc::mbar_wait_bounded(&a_empty[uint32_t(last_commit) % TC_SA],
                                           (uint32_t(last_commit) / TC_SA) & 1u, limit);
             }
+        }
+    } else if (warp == TC_TMA_WARP) {
+        // ------------------------------------- TMA of the vector operand (lane 0)
+        if (lane == 0) {
+            // slice j goes to stage j % TC_SB once the MMAs of slice j - TC_SB
+            // (same stage) are complete: up to TC_SB slices ahead of the MMAs
+            uint32_t j = 0;
+            bool ok = true;
+            for (int ui = u_begin; ui < u_end && ok; ++ui) {
+                const WorkUnit wu = a.units[ui];
+                const int nsteps = (wu.k1 - wu.k0) / TC_BK;
+                for (int s = 0; s < nsteps; ++s, ++j) {
+                    const int bs = int(j % TC_SB);
+                    if (j >= uint32_t(TC_SB) &&
+                        !tc::mbar_wait_or_abort(&a_empty[bs], ((j / TC_SB) - 1) & 1u, limit, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    unsigned char *B_hi = sm + L::B_OFF + bs * L::B_STAGE;
+                    const int32_t x = int32_t(int64_t(wu.k0) + int64_t(s) * TC_BK);
+                    tc::mbar_arrive_expect_tx(&b_full[bs], 2u * L::B_BYTES);
+                    tc::tma_load_2d(B_hi, &a.tm_b_hi, x, int32_t(n0), &b_full[bs]);
+                    tc::tma_load_2d(B_hi + L::B_BYTES, &a.tm_b_lo, x, int32_t(n0), &b_full[bs]);
+                }
+            }
+            if (!ok) *abort_flag = 1;
+            // nothing may still target this CTA's memory when it exits: wait
+            // for the last copy of every stage (no later copy of the stage was
+            // issued, so its phase cannot move on)
+            for (uint32_t k = j > uint32_t(TC_SB) ? j - TC_SB : 0u; k < j; ++k)
+                tc::mbar_wait_bounded(&b_full[k % TC_SB], (k / TC_SB) & 1u, limit);
         }
     } else {
         // ---------------------------------------------------------- epilogue
@@ -517,12 +533,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(const __grid_constant
                 break;
             }
             tc::tc_fence_after_sync();
-#pragma unroll
+#pragma unroll 1
             for (int c0 = 0; c0 < BN; c0 += 32) {
-                uint32_t r[32];
-                tc::tmem_ld_32x32b_x32(tmem + (uint32_t(32 * q) << 16) + uint32_t(acc * L::ACC_COLS + c0), r);
+                uint32_t r[16], r2[16];
+                const uint32_t t = tmem + (uint32_t(32 * q) << 16) + uint32_t(acc * L::ACC_COLS + c0);
+                tc::tmem_ld_32x32b_x16(t, r);
+                tc::tmem_ld_32x32b_x16(t + 16, r2);
+                tc::tmem_wait_ld(r, r2);
 #pragma unroll
-                for (int k = 0; k < 32; ++k) dst[(c0 + k) * TILE_R] = __uint_as_float(r[k]);
+                for (int k = 0; k < 16; ++k) {
+                    dst[(c0 + k) * TILE_R] = __uint_as_float(r[k]);
+                    dst[(c0 + 16 + k) * TILE_R] = __uint_as_float(r2[k]);
+                }
             }
             tc::tc_fence_before_sync();
             __syncwarp();
