@@ -60,11 +60,11 @@ static_assert(TC_SA == TC_SB, "the B copy of slice g + 2 reuses the stage of sli
 
 template <int BN>
 struct TcLayout {
-    static constexpr int A_BYTES = TILE_R * TC_BK * 2;               // 16 KB, one bf16 part
+    // shared memory: the B stages (TMA, 128-byte swizzle), the 8 x 8
+    // transposes of the adjoint's producers, the per-slice tables, barriers
     static constexpr int B_BYTES = BN * TC_BK * 2;
-    static constexpr int A_STAGE = 2 * A_BYTES;                      // hi + lo
-    static constexpr int B_STAGE = 2 * B_BYTES;
-    static constexpr int B_OFF = TC_SA * A_STAGE;
+    static constexpr int B_STAGE = 2 * B_BYTES;                      // hi + lo
+    static constexpr int B_OFF = 0;
     static constexpr int STG_OFF = B_OFF + TC_SB * B_STAGE;
     static constexpr int STAGING_BYTES = (TC_PROD / 8) * 8 * 9 * 4;  // 8x8 transposes (+pad)
     static constexpr int TAB_OFF = STG_OFF + STAGING_BYTES;          // per-slice tables
@@ -72,10 +72,19 @@ struct TcLayout {
     static constexpr int BAR_OFF = TAB_OFF + TAB_BYTES;
     static constexpr int NBARS = 2 * TC_SA + TC_SB + 4;              // a_full, a_empty, b_full, acc_full[2], acc_empty[2]
     static constexpr int CTRL_BYTES = NBARS * 8 + 16;                // + tensor-memory holder, abort flag
-    static constexpr int TOTAL = 1024 + BAR_OFF + CTRL_BYTES;
-    static constexpr int ACC_COLS = BN;                              // one accumulator (BN >= 32)
-    static constexpr int TMEM_COLS = 2 * ACC_COLS;                   // two, a power of two
-    static_assert(BN >= 32 && TMEM_COLS <= 512, "tensor memory");
+    // at least 117 KB, so that two CTAs never share an SM (and its tensor
+    // memory, of which one CTA takes up to all 512 columns)
+    static constexpr int USED = 1024 + BAR_OFF + CTRL_BYTES;
+    static constexpr int TOTAL = USED > 117 * 1024 ? USED : 117 * 1024;
+    // tensor memory: two accumulators of BN columns, then the A stages (hi
+    // and lo parts of 128 rows x 64 bf16, 32 columns each)
+    static constexpr int ACC_COLS = BN;
+    static constexpr int A_COL = 2 * ACC_COLS;
+    static constexpr int A_PART_COLS = TC_BK / 2;
+    static constexpr int A_STAGE_COLS = 2 * A_PART_COLS;
+    static constexpr int TMEM_NEED = A_COL + TC_SA * A_STAGE_COLS;
+    static constexpr int TMEM_COLS = TMEM_NEED <= 256 ? 256 : 512;   // a power of two
+    static_assert(BN >= 32 && TMEM_NEED <= 512, "tensor memory");
     static_assert(TOTAL <= 227 * 1024, "shared memory per CTA");
     static_assert(B_OFF % 1024 == 0 && B_STAGE % 1024 == 0 && B_BYTES % 1024 == 0, "swizzle atoms");
 };
@@ -369,8 +378,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(const __grid_constant
                     if (s + 3 < nsteps) put_tab(s + 3, true);
                     tc::cp_async_commit();
                 }
-                unsigned char *A_hi = sm + st * L::A_STAGE;
-                unsigned char *A_lo = A_hi + L::A_BYTES;
+                // this warp's lane quarter of the stage's hi part (lo: + 32 columns)
+                const uint32_t a_hi = tmem + (uint32_t(32 * (warp & 3)) << 16) +
+                                      uint32_t(L::A_COL + st * L::A_STAGE_COLS);
+                // the MMAs that read this stage before are complete (a_empty)
+                tc::tc_fence_after_sync();
                 const int64_t k0 = int64_t(wu.k0) + int64_t(s) * TC_BK;
                 const int w = s % TC_WIN;
                 float ac[QRUNS];
@@ -407,11 +419,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(const __grid_constant
                     }
                     uint4 hi, lo;
                     split_pack(v8, hi, lo);
-                    *reinterpret_cast<uint4 *>(A_hi + tc::sw128_chunk(row, chunk)) = hi;
-                    *reinterpret_cast<uint4 *>(A_lo + tc::sw128_chunk(row, chunk)) = lo;
+                    // row = 32 (warp mod 4) + lane: the warp's own lane quarter;
+                    // 8 bf16 of the chunk = 4 columns
+                    (void)row;
+                    __syncwarp();
+                    tc::tmem_st_32x32b_x4(a_hi + uint32_t(chunk * 4), hi);
+                    tc::tmem_st_32x32b_x4(a_hi + uint32_t(L::A_PART_COLS + chunk * 4), lo);
                 }
-                // the generic-proxy stores become visible to the tensor core
-                tc::fence_proxy_async_smem();
+                // the stores are complete before the MMA thread learns of them
+                tc::tmem_wait_st();
+                tc::tc_fence_before_sync();
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(&a_full[st]);
             }
@@ -424,12 +441,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(const __grid_constant
         // --------------------------------------------------- MMA issue (lane 0)
         if (lane == 0) {
             // hi*hi + hi*lo + lo*hi for each of the slice's four K steps of
-            // 16.  The stages sit at fixed strides, so a stage's operand
-            // descriptors are the first stage's plus a multiple of the stride
+            // 16, A from tensor memory (8 columns per step), B from shared
+            // memory.  The B stages sit at a fixed stride, so a stage's
+            // descriptor is the first stage's plus a multiple of the stride
             // (start-address field in 16-byte units; every shared-memory
             // address is below 2^18 bytes, so the field never carries).
             constexpr uint32_t IDESC = tc::idesc_bf16_f32(TILE_R, BN);
-            const uint64_t da0 = tc::desc_kmajor_sw128(tc::smem_u32(sm));
             const uint64_t db0 = tc::desc_kmajor_sw128(tc::smem_u32(sm + L::B_OFF));
             uint32_t g = 0, au = 0;
             int64_t last_commit = -1;
@@ -451,16 +468,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(const __grid_constant
                     if (!tc::mbar_wait_or_abort(&a_full[st], (g / TC_SA) & 1u, limit, abort_flag)) { ok = false; break; }
                     tc::tc_fence_after_sync();
                     if (!a.skip_mma) {
-                        const uint64_t ah = da0 + uint64_t(st) * uint64_t(L::A_STAGE >> 4);
-                        const uint64_t al = ah + uint64_t(L::A_BYTES >> 4);
+                        const uint32_t ah = tmem + uint32_t(L::A_COL + st * L::A_STAGE_COLS);
+                        const uint32_t al = ah + uint32_t(L::A_PART_COLS);
                         const uint64_t bh = db0 + uint64_t(st) * uint64_t(L::B_STAGE >> 4);
                         const uint64_t bl = bh + uint64_t(L::B_BYTES >> 4);
 #pragma unroll
                         for (int kk = 0; kk < TC_BK / 16; ++kk) {
                             const uint32_t acc0 = (s > 0 || kk > 0) ? 1u : 0u;   // 16 bf16 = 32 B per step
-                            tc::mma_bf16(d_tmem, ah + 2 * kk, bh + 2 * kk, IDESC, acc0);
-                            tc::mma_bf16(d_tmem, ah + 2 * kk, bl + 2 * kk, IDESC, 1u);
-                            tc::mma_bf16(d_tmem, al + 2 * kk, bh + 2 * kk, IDESC, 1u);
+                            tc::mma_bf16_ts(d_tmem, ah + 8 * kk, bh + 2 * kk, IDESC, acc0);
+                            tc::mma_bf16_ts(d_tmem, ah + 8 * kk, bl + 2 * kk, IDESC, 1u);
+                            tc::mma_bf16_ts(d_tmem, al + 8 * kk, bh + 2 * kk, IDESC, 1u);
                         }
                         // frees the A and the B stage of this slice
                         tc::mma_commit(&a_empty[st]);
