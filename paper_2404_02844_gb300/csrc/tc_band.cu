@@ -48,15 +48,15 @@
 namespace tomo {
 
 constexpr int TC_BK = 64;            // reduction slice per stage (one 128-byte bf16 row)
-constexpr int TC_SA = 3;             // A (weight) stages
-constexpr int TC_SB = 3;             // B (vector) stages, filled by TMA
+constexpr int TC_SA = 4;             // A (weight) stages, in tensor memory
+constexpr int TC_SB = 4;             // B (vector) stages, filled by TMA
 constexpr int TC_PROD = 512;         // producer threads (warps 0-15)
 constexpr int TC_MMA_WARP = 16;      // MMA issue
 constexpr int TC_TMA_WARP = 17;      // TMA of the vector operand
 constexpr int TC_THREADS = 22 * 32;  // + epilogue warps 18-21
 constexpr uint32_t TC_WAIT_LIMIT = 1u << 24;
 constexpr int TC_WIN = 4;            // windows of the per-slice tables (filled three slices ahead)
-static_assert(TC_SA == TC_SB, "the B copy of slice g + 2 reuses the stage of slice g - 1");
+static_assert(TC_SA == TC_SB, "one commit frees a slice's A and B stage");
 
 template <int BN>
 struct TcLayout {
@@ -66,7 +66,7 @@ struct TcLayout {
     static constexpr int B_STAGE = 2 * B_BYTES;                      // hi + lo
     static constexpr int B_OFF = 0;
     static constexpr int STG_OFF = B_OFF + TC_SB * B_STAGE;
-    static constexpr int STAGING_BYTES = (TC_PROD / 8) * 8 * 9 * 4;  // 8x8 transposes (+pad)
+    static constexpr int STAGING_BYTES = 2 * (TC_PROD / 8) * 8 * 9 * 4;  // 8x8 transposes of both runs (+pad)
     static constexpr int TAB_OFF = STG_OFF + STAGING_BYTES;          // per-slice tables
     static constexpr int TAB_BYTES = TC_WIN * TC_BK * (8 + 24) + (TILE_R + RUN) * 8;
     static constexpr int BAR_OFF = TAB_OFF + TAB_BYTES;
@@ -389,42 +389,55 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(const __grid_constant
 #pragma unroll
                 for (int q = 0; q < QRUNS; ++q) ac[q] = anc[q];
                 if (s + 1 < nsteps) fetch_anchors(s + 1);
+                // both runs of the thread: weights, the adjoint's transposes,
+                // the hi/lo split, then the tensor-memory stores (independent
+                // work interleaved, one warp synchronisation per step)
+                static_assert(QRUNS == 2, "two runs per producer thread");
+                float v8[QRUNS][RUN];
+                int chunk[QRUNS];
 #pragma unroll
                 for (int q = 0; q < QRUNS; ++q) {
                     const int run = tid + q * TC_PROD;
-                    float v8[RUN];
-                    int row, chunk;
                     if (FWD) {
-                        // row = probe r0 + row, chunk = photon numbers k0 + 8 chunk .. + 7
-                        row = run % TILE_R;
-                        chunk = run / TILE_R;
-                        tc_expand_run(ac[q], my.lam, my.lo, my.hi, int32_t(k0) + chunk * RUN, &win_r[w][chunk * RUN], v8);
+                        // row = probe r0 + run % 128 (= 32 (warp mod 4) + lane),
+                        // chunk = photon numbers k0 + 8 chunk .. + 7
+                        chunk[q] = run / TILE_R;
+                        tc_expand_run(ac[q], my.lam, my.lo, my.hi, int32_t(k0) + chunk[q] * RUN,
+                                      &win_r[w][chunk[q] * RUN], v8[q]);
                     } else {
                         // 8 x 8 block (8 probes x 8 photon numbers) per group of 8
-                        // lanes, transposed through shared memory so that one lane
-                        // holds 8 consecutive probes of one photon number
+                        // lanes: lane t expands probe kb 8 + t over the photon
+                        // numbers pb 8 .. + 7
                         const int g8 = run >> 3, t = run & 7;
                         const int pb = g8 % (TILE_R / 8), kb = g8 / (TILE_R / 8);
-                        row = pb * 8 + t;
-                        chunk = kb;
-                        float w8[RUN];
+                        chunk[q] = kb;
                         const ProbeMeta &m = win_m[w][kb * 8 + t];
+                        float w8[RUN];
                         tc_expand_run(ac[q], m.lam, m.lo, m.hi, int32_t(r0) + pb * 8, &rtile[pb * 8], w8);
 #pragma unroll
-                        for (int j = 0; j < RUN; ++j) stg[t * 9 + j] = w8[j];
-                        __syncwarp();
-#pragma unroll
-                        for (int j = 0; j < RUN; ++j) v8[j] = stg[j * 9 + t];
-                        __syncwarp();
+                        for (int j = 0; j < RUN; ++j) stg[q * (TC_PROD * 9) + t * 9 + j] = w8[j];
                     }
-                    uint4 hi, lo;
-                    split_pack(v8, hi, lo);
-                    // row = 32 (warp mod 4) + lane: the warp's own lane quarter;
-                    // 8 bf16 of the chunk = 4 columns
-                    (void)row;
+                }
+                if (!FWD) {
+                    // transposed through shared memory: lane t then holds the 8
+                    // probes kb 8 .. + 7 of photon number pb 8 + t (its row)
                     __syncwarp();
-                    tc::tmem_st_32x32b_x4(a_hi + uint32_t(chunk * 4), hi);
-                    tc::tmem_st_32x32b_x4(a_hi + uint32_t(L::A_PART_COLS + chunk * 4), lo);
+                    const int t = tid & 7;
+#pragma unroll
+                    for (int q = 0; q < QRUNS; ++q)
+#pragma unroll
+                        for (int j = 0; j < RUN; ++j) v8[q][j] = stg[q * (TC_PROD * 9) + j * 9 + t];
+                    __syncwarp();
+                }
+                uint4 hi[QRUNS], lo[QRUNS];
+#pragma unroll
+                for (int q = 0; q < QRUNS; ++q) split_pack(v8[q], hi[q], lo[q]);
+                // the warp's own lane quarter; 8 bf16 of a chunk = 4 columns
+                __syncwarp();
+#pragma unroll
+                for (int q = 0; q < QRUNS; ++q) {
+                    tc::tmem_st_32x32b_x4(a_hi + uint32_t(chunk[q] * 4), hi[q]);
+                    tc::tmem_st_32x32b_x4(a_hi + uint32_t(L::A_PART_COLS + chunk[q] * 4), lo[q]);
                 }
                 // the stores are complete before the MMA thread learns of them
                 tc::tmem_wait_st();
