@@ -504,6 +504,46 @@ def test_bounded_tensor_core_waits_report_a_timeout_and_leave_the_plan_usable(to
         assert tomo.lib().tomo_selftest_tc_timeout(pl._h) == 1   # EINVAL: not the tensor-core form
 
 
+def test_fit_batched_largest_c4_instance_checked_by_the_oracle(tomo):
+    """The corner of the batched distribution (instance 178, the largest of
+    the first 256: M = 8063, N = 127, D = 16126; 1237 photon numbers above
+    the last probe's band) at its four regularisation weights in one batched
+    call of the chosen (tensor-core) form, to KKT 1e-8.  The oracle, in FP64
+    on the CPU, re-evaluates every result that stopped on its KKT test: the
+    objective (Eq. min) agrees with the GPU's FP64 report to 1e-10, the KKT
+    residual of App. B from the oracle's own gradient equals the report's and
+    is within 1.5x the tolerance, and the result is on the simplices.  The better-conditioned weights (gamma >=
+    1e-2) must stop on the KKT test within the time bound."""
+    w = workloads.config_c4_instance(178)
+    assert (w.M, w.N, w.D) == (8063, 127, 16126)
+    P = dev(w.P)
+    problems, thetas = [], []
+    for g in workloads.C4_GAMMAS:
+        Th = torch.empty(w.M, w.N, dtype=torch.float64, device="cuda")
+        problems.append((w.M, w.N, w.lam, w.band_k, g, P, Th))
+        thetas.append(Th)
+    sts, reps = tomo.fit_batched(problems, precision="tc", concurrency=len(problems),
+                                 eps_kkt=1e-8, max_newton=3000, max_seconds=150.0)
+    checked = []
+    for g, Th, st, rep in zip(workloads.C4_GAMMAS, thetas, sts, reps):
+        T = host(Th)
+        assert np.abs(T.sum(1) - 1).max() <= 1e-12 and T.min() >= 0.0
+        if rep["stop_name"] != "kkt":
+            assert g < 1e-2, (g, rep)
+            continue
+        pr = oracle.Problem(w.M, w.N, w.lam, w.band_k, g)
+        f, G = pr.gradient(w.P, T)
+        assert abs(f - rep["f"]) <= 1e-10 * f, (g, f, rep["f"])
+        # the report's KKT residual is the final FP64 one (the stopping test
+        # ran on the form's own gradient): the oracle's equals it, and stays
+        # within 1.5x the tolerance
+        k = pr.kkt(T, G)
+        assert k == pytest.approx(rep["kkt"], rel=1e-9), (g, k, rep["kkt"])
+        assert k <= 1.5e-8, (g, k)
+        checked.append(g)
+    assert {1e-2, 1e-1} <= set(checked), checked
+
+
 @pytest.mark.parametrize("prec", ["tc", "fp32"])
 def test_fit_batched_largest_c4_instance_reaches_the_oracle_optimum(tomo, prec):
     """The corner of the batched distribution (instance 178: M = 8063, N =
