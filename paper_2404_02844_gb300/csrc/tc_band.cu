@@ -51,6 +51,7 @@ constexpr int TC_BK = 64;            // reduction slice per stage (one 128-byte 
 constexpr int TC_SA = 4;             // A (weight) stages, in tensor memory
 constexpr int TC_SB = 4;             // B (vector) stages, filled by TMA
 constexpr int TC_PROD = 512;         // producer threads (warps 0-15)
+constexpr int TC_PW = TC_PROD / 32;  // producer warps
 constexpr int TC_MMA_WARP = 16;      // MMA issue
 constexpr int TC_TMA_WARP = 17;      // TMA of the vector operand
 constexpr int TC_THREADS = 22 * 32;  // + epilogue warps 18-21
@@ -68,7 +69,13 @@ struct TcLayout {
     static constexpr int STG_OFF = B_OFF + TC_SB * B_STAGE;
     static constexpr int STAGING_BYTES = 2 * (TC_PROD / 8) * 8 * 9 * 4;  // 8x8 transposes of both runs (+pad)
     static constexpr int TAB_OFF = STG_OFF + STAGING_BYTES;          // per-slice tables
-    static constexpr int TAB_BYTES = TC_WIN * TC_BK * (8 + 24) + (TILE_R + RUN) * 8;
+    // per producer warp: TC_WIN windows of 16 table entries (the forward's
+    // ratio pairs, 8 bytes, and the adjoint's probe metadata, 24 bytes) and
+    // the adjoint's 32 ratio pairs of its rows
+    static constexpr int TAB_R_OFF = 0;
+    static constexpr int TAB_M_OFF = TAB_R_OFF + TC_PW * TC_WIN * 16 * 8;
+    static constexpr int TAB_T_OFF = TAB_M_OFF + TC_PW * TC_WIN * 16 * 24;
+    static constexpr int TAB_BYTES = TAB_T_OFF + TC_PW * 32 * 8;
     static constexpr int BAR_OFF = TAB_OFF + TAB_BYTES;
     static constexpr int NBARS = 2 * TC_SA + TC_SB + 4;              // a_full, a_empty, b_full, acc_full[2], acc_empty[2]
     static constexpr int CTRL_BYTES = NBARS * 8 + 16;                // + tensor-memory holder, abort flag
@@ -195,21 +202,6 @@ __device__ __forceinline__ void tc_expand_run(float v, float2 lam, int32_t lo, i
     }
 }
 
-// Barrier of the producer threads (named barrier 1) that also returns
-// the OR of their flags: every producer reaches it once per slice after
-// bounded waits only, so it cannot hold a producer forever.
-__device__ __forceinline__ bool producers_sync_or(bool v)
-{
-    uint32_t r;
-    asm volatile(
-        "{\n\t.reg .pred pi, po;\n\t"
-        "setp.ne.u32 pi, %1, 0;\n\t"
-        "bar.red.or.pred po, 1, %2, pi;\n\t"
-        "selp.u32 %0, 1, 0, po;\n\t}"
-        : "=r"(r) : "r"(uint32_t(v)), "n"(TC_PROD) : "memory");
-    return r != 0;
-}
-
 // Packs 8 floats into hi and lo bf16 chunks (hi = rn(v), lo = rn(v - hi)),
 // two values per conversion instruction.
 __device__ __forceinline__ void split_pack(const float (&v)[8], uint4 &hi, uint4 &lo)
@@ -281,22 +273,29 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(const __grid_constant
 
     if (warp < TC_MMA_WARP) {
         // ------------------------------------------------------------ producers
-        // Per-slice tables live in shared memory windows, filled three slices
-        // ahead by the first 64 producer threads with asynchronous copies (no
-        // register waits on the critical path): the forward's ratios 1/(i+1)
-        // of the slice's photon numbers, the adjoint's probe metadata of the
-        // slice's probes (its ratios cover the whole tile and are loaded per
-        // unit).  A copy group is committed every slice; waiting for all but
-        // the latest before the slice barrier publishes the tables of the next
-        // slice.  Producer-wide agreement (tables written, a wait given up)
-        // goes through one bounded barrier with an OR reduction per slice.
+        // Every producer warp keeps its own tables in shared memory, so the
+        // warps never wait for one another: windows of the 16 entries its two
+        // runs per thread need (the forward's ratio pairs 1/(i+1) of its two
+        // chunks of photon numbers, the adjoint's metadata of its 16 probes),
+        // filled three slices ahead by lanes 0-15 with asynchronous copies,
+        // and for the adjoint the ratio pairs of its 32 rows, per unit.  A
+        // copy group is committed every slice; waiting for all but the latest
+        // (then __syncwarp) publishes the tables of the next slice.  A warp
+        // that gives up raises the abort flag; the others meet it in their
+        // own bounded waits.
         constexpr int QRUNS = (TILE_R * TC_BK / RUN) / TC_PROD;       // 2 runs of 8 per thread
         static_assert(QRUNS * TC_PROD == TILE_R * TC_BK / RUN, "runs per producer");
+        static_assert(QRUNS * 8 == 16, "16 table entries per producer warp");
         float *stg = staging + ((tid >> 3) * 8) * 9;
-        float2 (*win_r)[TC_BK] = reinterpret_cast<float2 (*)[TC_BK]>(sm + L::TAB_OFF);
-        ProbeMeta (*win_m)[TC_BK] = reinterpret_cast<ProbeMeta (*)[TC_BK]>(sm + L::TAB_OFF + TC_WIN * TC_BK * 8);
-        float2 *rtile = reinterpret_cast<float2 *>(sm + L::TAB_OFF + TC_WIN * TC_BK * (8 + 24));
+        float2 (*win_r)[16] = reinterpret_cast<float2 (*)[16]>(sm + L::TAB_OFF + L::TAB_R_OFF) + warp * TC_WIN;
+        ProbeMeta (*win_m)[16] = reinterpret_cast<ProbeMeta (*)[16]>(sm + L::TAB_OFF + L::TAB_M_OFF) + warp * TC_WIN;
+        float2 *rtile = reinterpret_cast<float2 *>(sm + L::TAB_OFF + L::TAB_T_OFF) + warp * 32;
         const ProbeMeta none{1, 0, 0, make_float2(0.f, 0.f)};
+        // this thread's runs: row 32 (warp mod 4) + lane of the tile, and
+        // reduction chunks (8 photon numbers, forward; 8 probes, adjoint)
+        // warp / 4 + 4 q; table entry q * 8 + (lane mod 8) of a window
+        const int row = 32 * (warp & 3) + lane;
+        const int t8 = lane & 7;
         uint32_t g = 0;
         bool ok = true;
         for (int ui = u_begin; ui < u_end && ok; ++ui) {
@@ -304,22 +303,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(const __grid_constant
             const int nsteps = (wu.k1 - wu.k0) / TC_BK;
             if (nsteps == 0) continue;
             const int64_t r0 = int64_t(wu.tile) * TILE_R;
-            // forward: every thread expands runs of one probe (row tid % 128)
-            const ProbeMeta my = FWD ? load_meta(a, r0 + (tid % TILE_R)) : none;
-            // entry tid (< 64) of the table of slice j, synchronously or by
-            // asynchronous copies (entries outside the range are written
-            // directly; the slot belongs to this thread alone)
+            // forward: every thread expands runs of one probe (its row)
+            const ProbeMeta my = FWD ? load_meta(a, r0 + row) : none;
+            // entry `lane` (< 16) of this warp's table of slice j, synchronously
+            // or by asynchronous copies (entries outside the range are written
+            // directly; the slot belongs to this lane alone)
             auto put_tab = [&](int j, bool async) {
                 const int64_t k0j = int64_t(wu.k0) + int64_t(j) * TC_BK;
+                const int c = (warp >> 2) + 4 * (lane >> 3);
                 if (FWD) {
-                    float2 *dst = &win_r[j % TC_WIN][tid];
-                    const int64_t idx = k0j + tid + 1;
+                    float2 *dst = &win_r[j % TC_WIN][lane];
+                    const int64_t idx = k0j + c * RUN + t8 + 1;
                     if (idx > a.M + RUN) *dst = make_float2(0.f, 0.f);
                     else if (async) tc::cp_async<8>(dst, &a.rinv2[idx]);
                     else *dst = __ldg(&a.rinv2[idx]);
                 } else {
-                    ProbeMeta *dst = &win_m[j % TC_WIN][tid];
-                    const int64_t d = k0j + tid;
+                    ProbeMeta *dst = &win_m[j % TC_WIN][lane];
+                    const int64_t d = k0j + c * 8 + t8;
                     if (d >= wu.k1 || d >= a.D) {
                         *dst = none;
                     } else if (async) {
@@ -338,43 +338,39 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(const __grid_constant
                 const int64_t k0j = int64_t(wu.k0) + int64_t(j) * TC_BK;
 #pragma unroll
                 for (int q = 0; q < QRUNS; ++q) {
-                    const int run = tid + q * TC_PROD;
-                    if (FWD) {
-                        anc[q] = anchor_of(a.anchor, my, k0j + int64_t(run / TILE_R) * RUN);
-                    } else {
-                        const int g8 = run >> 3, t = run & 7;
-                        const int pb = g8 % (TILE_R / 8), kb = g8 / (TILE_R / 8);
-                        anc[q] = anchor_of(a.anchor, win_m[j % TC_WIN][kb * 8 + t], r0 + pb * 8);
-                    }
+                    const int c = (warp >> 2) + 4 * q;
+                    if (FWD) anc[q] = anchor_of(a.anchor, my, k0j + int64_t(c) * RUN);
+                    else anc[q] = anchor_of(a.anchor, win_m[j % TC_WIN][q * 8 + t8], r0 + (row & ~7));
                 }
             };
-            {   // prologue of the unit: tables of slices 0 to 2, the adjoint's ratios
-                // (after every producer is done with the previous unit's tables)
-                producers_sync_or(false);
-                if (tid < TC_BK)
+            {   // prologue of the unit: this warp's tables of slices 0 to 2 and
+                // the adjoint's ratios of its rows (the warp is done with the
+                // previous unit's tables)
+                __syncwarp();
+                if (lane < 16)
                     for (int j = 0; j < 3 && j < nsteps; ++j) put_tab(j, false);
-                if (!FWD)
-                    for (int k = tid; k < TILE_R + RUN; k += TC_PROD) {
-                        const int64_t idx = r0 + k + 1;
-                        rtile[k] = idx <= a.M + RUN ? __ldg(&a.rinv2[idx]) : make_float2(0.f, 0.f);
-                    }
-                producers_sync_or(false);
+                if (!FWD) {
+                    const int64_t idx = r0 + row + 1;
+                    rtile[lane] = idx <= a.M + RUN ? __ldg(&a.rinv2[idx]) : make_float2(0.f, 0.f);
+                }
+                __syncwarp();
                 fetch_anchors(0);
             }
             for (int s = 0; s < nsteps; ++s, ++g) {
                 const int st = int(g % TC_SA);
                 bool wok = true;
                 if (g >= TC_SA) wok = warp_wait(&a_empty[st], ((g / TC_SA) - 1) & 1u, limit, abort_flag);
-                // the tables of slice s + 1 (copies issued at slice s - 2) have
-                // landed; after the barrier every producer is past slice s - 1,
-                // so the window of slice s - 1 may take slice s + 3
-                if (tid < TC_BK) tc::cp_async_wait<1>();
-                if (producers_sync_or(!wok)) {
+                if (!wok) {
                     *abort_flag = 1;
                     ok = false;
                     break;
                 }
-                if (tid < TC_BK) {
+                // the warp's tables of slice s + 1 (copies issued at slice
+                // s - 2) have landed; the warp is past slice s - 1, so that
+                // window may take slice s + 3
+                if (lane < 16) tc::cp_async_wait<1>();
+                __syncwarp();
+                if (lane < 16) {
                     if (s + 3 < nsteps) put_tab(s + 3, true);
                     tc::cp_async_commit();
                 }
@@ -403,7 +399,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(const __grid_constant
                         // chunk = photon numbers k0 + 8 chunk .. + 7
                         chunk[q] = run / TILE_R;
                         tc_expand_run(ac[q], my.lam, my.lo, my.hi, int32_t(k0) + chunk[q] * RUN,
-                                      &win_r[w][chunk[q] * RUN], v8[q]);
+                                      &win_r[w][q * 8], v8[q]);
                     } else {
                         // 8 x 8 block (8 probes x 8 photon numbers) per group of 8
                         // lanes: lane t expands probe kb 8 + t over the photon
@@ -411,9 +407,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(const __grid_constant
                         const int g8 = run >> 3, t = run & 7;
                         const int pb = g8 % (TILE_R / 8), kb = g8 / (TILE_R / 8);
                         chunk[q] = kb;
-                        const ProbeMeta &m = win_m[w][kb * 8 + t];
+                        const ProbeMeta &m = win_m[w][q * 8 + t];
                         float w8[RUN];
-                        tc_expand_run(ac[q], m.lam, m.lo, m.hi, int32_t(r0) + pb * 8, &rtile[pb * 8], w8);
+                        tc_expand_run(ac[q], m.lam, m.lo, m.hi, int32_t(r0) + pb * 8,
+                                      &rtile[(pb - 4 * (warp & 3)) * 8], w8);
 #pragma unroll
                         for (int j = 0; j < RUN; ++j) stg[q * (TC_PROD * 9) + t * 9 + j] = w8[j];
                     }
@@ -447,9 +444,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(const __grid_constant
             }
             // no copy may still be in flight into a window the next unit's
             // prologue rewrites
-            if (tid < TC_BK) tc::cp_async_wait<0>();
+            if (lane < 16) tc::cp_async_wait<0>();
         }
-        if (tid < TC_BK) tc::cp_async_wait<0>();
+        if (lane < 16) tc::cp_async_wait<0>();
     } else if (warp == TC_MMA_WARP) {
         // --------------------------------------------------- MMA issue (lane 0)
         if (lane == 0) {
