@@ -7,7 +7,8 @@
 //                        over the probes whose band meets the tile;
 //   HVP = 2 F^T (F u) + 2 gamma L u (Table ops, Hessian products).
 //
-// Operands are bf16 in shared memory, K-major, 128-byte swizzled; the
+// Operands are bf16: the weights (A) in tensor memory, 128 lanes = tile rows;
+// the vector operand (B) in shared memory, K-major, 128-byte swizzled; the
 // accumulator is f32 in tensor memory.  Precision is recovered by splitting
 // every operand into hi + lo bf16 parts and accumulating hi*hi + hi*lo +
 // lo*hi (three MMAs per K step of 16 into one accumulator, ~17 significant
@@ -17,15 +18,17 @@
 // The contraction kernel is warp-specialised and persistent (one CTA per SM,
 // a list of work units each):
 //   producer warps 0-15 generate the Poisson weights of every 64-wide slice
-//                       straight into a ring of A stages (runs of 8 photon
-//                       numbers from the log-space anchors, exact ratio
-//                       recurrence in float) and signal them on an mbarrier;
+//                       straight into a ring of four A stages in tensor
+//                       memory (runs of 8 photon numbers from the log-space
+//                       anchors, exact ratio recurrence in float; each warp
+//                       writes its own lane quarter) and signal them on an
+//                       mbarrier;
 //   warp 16             issues the slice's MMAs into one of two tensor-memory
 //                       accumulators and commits them to the barriers that
 //                       free the stages and publish a finished unit;
 //   warp 17             loads the vector operand of each slice by TMA from a
 //                       transposed bf16 hi/lo copy (rows = outcomes,
-//                       contiguous along the reduction index), up to three
+//                       contiguous along the reduction index), up to four
 //                       slices ahead of the MMAs;
 //   warps 18-21         move each finished accumulator to the unit's f32
 //                       partial tile (column-major, coalesced stores) while
