@@ -1,7 +1,8 @@
 // tc_ptx.cuh -- inline-PTX wrappers for the Blackwell (sm_100a/sm_103a) 5th-
-// generation tensor cores: tensor-memory allocation, tcgen05.mma with shared-
-// memory matrix descriptors, completion tracking through mbarriers, and
-// tensor-memory loads for the epilogue.  Every wait is bounded.
+// generation tensor cores: tensor-memory allocation, stores and loads,
+// tcgen05.mma with A in tensor memory and B by shared-memory matrix
+// descriptor, TMA tiles and small asynchronous copies, and completion
+// tracking through mbarriers.  Every wait is bounded.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -32,11 +33,6 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
 }
 
 // ---- fences -----------------------------------------------------------------
-// generic-proxy shared-memory writes -> visible to the tensor core (async proxy)
-__device__ __forceinline__ void fence_proxy_async_smem()
-{
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
 __device__ __forceinline__ void tc_fence_before_sync()
 {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -158,20 +154,9 @@ __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N)
            | (uint32_t(M >> 4) << 24);     // M / 16
 }
 
-// D[tmem] (+)= A[smem desc] x B[smem desc]^T, issued by one thread.
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
-                                         uint32_t idesc, uint32_t accumulate)
-{
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-        :: "r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate) : "memory");
-}
-
-// The same with A in tensor memory (128 lanes = rows, K packed two bf16 per
-// 32-bit column, lower index in the low half): only B is read from shared
-// memory.
+// D[tmem] (+)= A[tmem] x B[smem desc]^T, issued by one thread: A in tensor
+// memory (128 lanes = rows, K packed two bf16 per 32-bit column, lower index
+// in the low half), B a K-major shared-memory tile.
 __device__ __forceinline__ void mma_bf16_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc,
                                             uint32_t idesc, uint32_t accumulate)
 {
@@ -228,13 +213,6 @@ __device__ __forceinline__ void tmem_wait_ld(uint32_t (&a)[16], uint32_t (&b)[16
                    "+r"(b[7]), "+r"(b[8]), "+r"(b[9]), "+r"(b[10]), "+r"(b[11]), "+r"(b[12]),
                    "+r"(b[13]), "+r"(b[14]), "+r"(b[15])
                  :: "memory");
-}
-
-// Byte offset of the 16-byte chunk c (0..7) of row r in a K-major 128-byte-
-// swizzled tile (rows at 128 B, chunks permuted by XOR with r mod 8).
-__device__ __forceinline__ uint32_t sw128_chunk(int r, int c)
-{
-    return uint32_t((r >> 3) * 1024 + (r & 7) * 128 + ((c ^ (r & 7)) << 4));
 }
 
 }  // namespace tc
