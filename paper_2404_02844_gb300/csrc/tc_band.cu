@@ -1055,7 +1055,7 @@ size_t tc_smem_bytes(int bn)
 
 // Tensor map of a transposed bf16 operand copy (rows x pitch elements, pitch
 // a multiple of 64): boxes of 64 elements x bn rows with the 128-byte swizzle
-// of the MMA operand layout.  The driver's encoder is looked up once.
+// of the MMA operand layout.  The CUDA driver API's encoder is looked up once.
 cudaError_t encode_operand_map(CUtensorMap *map, const void *base, int64_t pitch, int64_t rows, int bn)
 {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
