@@ -79,7 +79,11 @@ struct TcLayout {
     static constexpr int TAB_M_OFF = TAB_R_OFF + TC_PW * TC_WIN * 16 * 8;
     static constexpr int TAB_T_OFF = TAB_M_OFF + TC_PW * TC_WIN * 16 * 24;
     static constexpr int TAB_BYTES = TAB_T_OFF + TC_PW * 32 * 8;
-    static constexpr int BAR_OFF = TAB_OFF + TAB_BYTES;
+    // forward: per producer warp, three windows of its lanes' anchors (two
+    // runs each), filled two slices ahead
+    static constexpr int ANC_OFF = TAB_OFF + TAB_BYTES;
+    static constexpr int ANC_BYTES = TC_PW * 3 * 2 * 32 * 4;
+    static constexpr int BAR_OFF = ANC_OFF + ANC_BYTES;
     static constexpr int NBARS = 2 * TC_SA + TC_SB + 4;              // a_full, a_empty, b_full, acc_full[2], acc_empty[2]
     static constexpr int CTRL_BYTES = NBARS * 8 + 16;                // + tensor-memory holder, abort flag
     // at least 117 KB, so that two CTAs never share an SM (and its tensor
@@ -299,6 +303,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(const __grid_constant
         // warp / 4 + 4 q; table entry q * 8 + (lane mod 8) of a window
         const int row = 32 * (warp & 3) + lane;
         const int t8 = lane & 7;
+        float (*wanc)[QRUNS][32] = reinterpret_cast<float (*)[QRUNS][32]>(sm + L::ANC_OFF) + warp * 3;
+        static_assert(QRUNS == 2, "anchor windows hold two runs per lane");
         uint32_t g = 0;
         bool ok = true;
         for (int ui = u_begin; ui < u_end && ok; ++ui) {
@@ -335,7 +341,27 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(const __grid_constant
                     }
                 }
             };
-            // the anchors of every run of slice j (tables of slice j in place)
+            // forward: the anchors of this lane's runs of slice j into window
+            // j % 3, by asynchronous copies or directly (a run that misses the
+            // band has weight 0: its slot is written directly)
+            auto put_anchors_fwd = [&](int j, bool async) {
+                const int64_t k0j = int64_t(wu.k0) + int64_t(j) * TC_BK;
+                const int64_t a0 = int64_t(my.lo) & ~int64_t(RUN - 1);
+#pragma unroll
+                for (int q = 0; q < QRUNS; ++q) {
+                    const int64_t i_r = k0j + int64_t((warp >> 2) + 4 * q) * RUN;
+                    float *dst = &wanc[j % 3][q][lane];
+                    if (i_r + RUN - 1 < my.lo || i_r > my.hi) {
+                        *dst = 0.f;
+                    } else {
+                        const float *src = &a.anchor[my.aoff + (i_r - a0) / RUN];
+                        if (async) tc::cp_async<4>(dst, src);
+                        else *dst = __ldg(src);
+                    }
+                }
+            };
+            // adjoint: the anchors of every run of slice j, one slice ahead in
+            // registers (tables of slice j in place)
             float anc[QRUNS];
             auto fetch_anchors = [&](int j) {
                 const int64_t k0j = int64_t(wu.k0) + int64_t(j) * TC_BK;
@@ -356,8 +382,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(const __grid_constant
                     const int64_t idx = r0 + row + 1;
                     rtile[lane] = idx <= a.M + RUN ? __ldg(&a.rinv2[idx]) : make_float2(0.f, 0.f);
                 }
+                if (FWD) {
+                    put_anchors_fwd(0, false);
+                    if (nsteps > 1) put_anchors_fwd(1, false);
+                }
                 __syncwarp();
-                fetch_anchors(0);
+                if (!FWD) fetch_anchors(0);
             }
             for (int s = 0; s < nsteps; ++s, ++g) {
                 const int st = int(g % TC_SA);
@@ -368,15 +398,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(const __grid_constant
                     ok = false;
                     break;
                 }
-                // the warp's tables of slice s + 1 (copies issued at slice
-                // s - 2) have landed; the warp is past slice s - 1, so that
-                // window may take slice s + 3
-                if (lane < 16) tc::cp_async_wait<1>();
+                // the copies issued at slice s - 2 have landed: the warp's
+                // tables of slice s + 1 and (forward) this lane's anchors of
+                // slice s; the warp is past slice s - 1, so its windows may
+                // take slice s + 3 (tables) and s + 2 (anchors).  One copy
+                // group per slice and thread.
+                tc::cp_async_wait<1>();
                 __syncwarp();
-                if (lane < 16) {
-                    if (s + 3 < nsteps) put_tab(s + 3, true);
-                    tc::cp_async_commit();
-                }
+                if (lane < 16 && s + 3 < nsteps) put_tab(s + 3, true);
+                if (FWD && s + 2 < nsteps) put_anchors_fwd(s + 2, true);
+                tc::cp_async_commit();
                 // this warp's lane quarter of the stage's hi part (lo: + 32 columns)
                 const uint32_t a_hi = tmem + (uint32_t(32 * (warp & 3)) << 16) +
                                       uint32_t(L::A_COL + st * L::A_STAGE_COLS);
@@ -385,9 +416,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(const __grid_constant
                 const int64_t k0 = int64_t(wu.k0) + int64_t(s) * TC_BK;
                 const int w = s % TC_WIN;
                 float ac[QRUNS];
+                if (FWD) {
 #pragma unroll
-                for (int q = 0; q < QRUNS; ++q) ac[q] = anc[q];
-                if (s + 1 < nsteps) fetch_anchors(s + 1);
+                    for (int q = 0; q < QRUNS; ++q) ac[q] = wanc[s % 3][q][lane];
+                } else {
+#pragma unroll
+                    for (int q = 0; q < QRUNS; ++q) ac[q] = anc[q];
+                    if (s + 1 < nsteps) fetch_anchors(s + 1);
+                }
                 // both runs of the thread: weights, the adjoint's transposes,
                 // the hi/lo split, then the tensor-memory stores (independent
                 // work interleaved, one warp synchronisation per step)
@@ -447,9 +483,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_tc(const __grid_constant
             }
             // no copy may still be in flight into a window the next unit's
             // prologue rewrites
-            if (lane < 16) tc::cp_async_wait<0>();
+            tc::cp_async_wait<0>();
         }
-        if (lane < 16) tc::cp_async_wait<0>();
+        tc::cp_async_wait<0>();
     } else if (warp == TC_MMA_WARP) {
         // --------------------------------------------------- MMA issue (lane 0)
         if (lane == 0) {
